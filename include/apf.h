@@ -1,0 +1,151 @@
+/*
+ * apf.h -- C ABI of the GB300 augmented-partial-factorization solver.
+ *
+ * Problem (paper Sec. 2, first paragraph and Fig. 1a): given the relative
+ * permittivity of a 2D TM structure, return the generalized scattering
+ * matrix S = C A^-1 B - D over many input and output channels, and the
+ * gradient of an objective f(S) with respect to the permittivity of every
+ * design pixel (Eq. 1 with Eqs. 2-4: dA/dp_k is diagonal and rank one for a
+ * pixel, so the whole gradient comes from C A^-1 U and U^T A^-1 B in the same
+ * elimination).
+ *
+ * Geometry and conventions
+ *   - Grid nx (periodic, x) by ny rows (y); unit pixel; vacuum wavelength
+ *     lambda_px pixels, k = 2 pi / lambda_px.  Rows [0, npml_bot) and
+ *     [ny - npml_top, ny) are graded PMLs: s(y) = 1 + i a (d/L)^p,
+ *     a = -(p+1) ln(R0) / (2 k sqrt(eps_side) L), d measured from the
+ *     half-integer interface row, Dirichlet walls beyond.
+ *   - A = -d2/dx2 - d/dy (1/s) d/dy - k^2 eps, multiplied through by s and by
+ *     dx^2 (complex symmetric; 5-point stencil).
+ *   - Substrate (eps_sub) fills rows below the slab, cladding (eps_clad)
+ *     rows above; the design slab is rows [j0, j0+h) with eps_slab[j][x].
+ *   - Channels: Fourier orders u_m(x) = exp(2 pi i m x/nx)/sqrt(nx).  Input a:
+ *     unit-flux source -2i sqrt(nu_a) u_{m_a} on row npml_bot; output b:
+ *     projection sqrt(nu_b) u_{m_b}^H on row ny-npml_top-1; nu = sin(k_y) of
+ *     the 5-point dispersion in the substrate / cladding; D = 0.
+ *   - Gradient: df/deps_k = 2 Re sum_{ba} Gamma_ba dS_ba/deps_k with
+ *     Gamma = df/dS the Wirtinger derivative (Eq. 1); dA/deps_k = -k^2.
+ *
+ * Memory
+ *   - All arrays are row-major.  Complex arrays are interleaved (re, im)
+ *     float64 pairs.  Array arguments may be host or device pointers (the
+ *     library asks the CUDA runtime which); results land where the pointer
+ *     points.  The caller owns all argument buffers; the context owns its
+ *     device workspace, allocated by the apf_set_* calls (never by a solve).
+ *   - A solve enqueues its kernels on `stream` (a cudaStream_t, NULL = the
+ *     legacy default stream) and synchronizes that stream before returning,
+ *     so host outputs are valid on return.
+ *
+ * Errors
+ *   - Every int-returning call returns APF_OK (0) or a negative APF_E* code;
+ *     apf_last_error() gives a one-line message for the most recent failure.
+ *   - Size/argument checks run on the host before any launch (APF_EINVAL).
+ *   - A context is single-threaded: calls on one context must not overlap.
+ */
+#ifndef APF_H
+#define APF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define APF_OK 0
+#define APF_EINVAL (-1)     /* bad argument, size, or non-finite permittivity */
+#define APF_ENOMEM (-2)     /* device allocation failed */
+#define APF_ESINGULAR (-3)  /* a zero pivot in a diagonal-block inversion */
+#define APF_ENOCONV (-4)    /* refinement stopped above tolerance (results returned) */
+#define APF_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define APF_ECUDA (-6)      /* CUDA runtime error */
+#define APF_ESTATE (-7)     /* call order: grid, permittivity or channels not set */
+
+/* Arithmetic of the slab elimination. */
+#define APF_FP64 0          /* everything in float64 */
+#define APF_MIXED_BF16X3 1  /* tensor-core bf16x3 products, fp32 accumulation,
+                               float64 iterative refinement of the fields */
+
+/* Objectives for apf_solve_S_grad (relative diffraction orders d = m_out - m_in). */
+#define APF_OBJ_POWER 1     /* f = sum_a sum_{d in D} |S_{a+d,a}|^2 */
+#define APF_OBJ_SPLITTER 2  /* f = sum_a sum_{d in D} (|S_{a+d,a}|^2 - t)^2   (Eq. 5) */
+
+typedef struct apf_ctx apf_ctx;
+
+typedef struct {
+    double R0;     /* normal-incidence PML round-trip reflection (default 1e-8) */
+    double power;  /* grading exponent p (default 3) */
+} apf_pml_params;
+
+typedef struct {
+    int refine_iters;       /* refinement sweeps taken by the last solve */
+    double residual;        /* max over columns of ||r||/||R|| after the last solve */
+    double ms_total;        /* device time of the last solve, milliseconds */
+    double ms_boundary;     /* per-mode boundary elimination + channel set-up */
+    double ms_eliminate;    /* slab block-Schur elimination (inversions) */
+    double ms_fields;       /* right-hand-side sweeps (+ refinement) */
+    double ms_readout;      /* S, f, Gamma */
+    double ms_gradient;     /* adjoint contraction */
+    long long kernel_launches; /* kernels launched by the last solve */
+    long long workspace_bytes; /* device bytes held by the context */
+} apf_stats;
+
+/* Create a context on CUDA device `cuda_device` with APF_FP64 or
+   APF_MIXED_BF16X3 arithmetic.  *out receives the handle (NULL on failure). */
+int apf_create(apf_ctx **out, int cuda_device, int precision);
+
+/* Free the context and its device workspace.  NULL is a no-op. */
+void apf_destroy(apf_ctx *ctx);
+
+/* Grid (paper Sec. 2 operator; readings in the header comment).  nx must be
+   a power of two in [8, 8192]; npml_bot, npml_top >= 1; lambda_px > 2.
+   pml may be NULL for the defaults.  Invalidates permittivity and channels. */
+int apf_set_grid(apf_ctx *ctx, int nx, int ny, int npml_bot, int npml_top,
+                 double lambda_px, const apf_pml_params *pml);
+
+/* Design slab and background media.  eps_slab: h*nx float64, [row][x],
+   host or device, real and finite.  j0 < 0 centres the slab between the
+   PMLs; otherwise the source row npml_bot < j0 and j0+h <= ny-npml_top-1. */
+int apf_set_eps(apf_ctx *ctx, const double *eps_slab, int j0, int h,
+                double eps_sub, double eps_clad);
+
+/* Channel orders (host int arrays).  NULL (or n = 0) selects every order
+   that propagates in the cladding (paper Sec. 3: all angles within the range
+   of interest, spaced 2 pi / W).  Inputs must propagate in the substrate,
+   outputs in the cladding.  Requires set_grid and set_eps. */
+int apf_set_channels(apf_ctx *ctx, const int *m_in, int n_in,
+                     const int *m_out, int n_out);
+
+/* Query the channel counts; m_in / m_out (host, may be NULL) receive the
+   orders (n_in resp. n_out ints). */
+int apf_get_channels(const apf_ctx *ctx, int *n_in, int *n_out, int *m_in, int *m_out);
+
+/* S = C A^-1 B (n_out x n_in complex128, [b][a]).  Keeps the slab fields so
+   that apf_grad_from_gamma can follow. */
+int apf_solve_S(apf_ctx *ctx, double *S, void *stream);
+
+/* S, f and df/deps (h*nx float64) for a built-in objective.
+   params = {t, nD, d_1, ..., d_nD} (as doubles), n_params = 2 + nD.
+   f is a host pointer (may be NULL); S and grad_eps may be host or device. */
+int apf_solve_S_grad(apf_ctx *ctx, int objective, const double *params, int n_params,
+                     double *S, double *f, double *grad_eps, void *stream);
+
+/* df/deps = 2 Re sum_ba Gamma_ba dS_ba/deps for a caller-supplied
+   Gamma = df/dS (n_out x n_in complex128), using the fields of the last
+   solve (Eq. 1 with Eq. 3).  grad_eps: h*nx float64. */
+int apf_grad_from_gamma(apf_ctx *ctx, const double *Gamma, double *grad_eps, void *stream);
+
+/* Iterative refinement of the mixed mode: stop when max_col ||r||/||R|| <= tol
+   or after max_iters sweeps (APF_ENOCONV if still above tol). */
+int apf_set_refinement(apf_ctx *ctx, double tol, int max_iters);
+
+int apf_get_stats(const apf_ctx *ctx, apf_stats *stats);
+
+/* Message of the most recent failure on this context (or of apf_create when
+   ctx is NULL).  Never NULL. */
+const char *apf_last_error(const apf_ctx *ctx);
+
+/* ABI version, (major << 16) | minor. */
+int apf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APF_H */

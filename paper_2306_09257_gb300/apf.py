@@ -1,0 +1,217 @@
+"""Python binding of libapf (ctypes): argument marshalling only.
+
+Every numerical step runs inside ``_lib/libapf.so``.  There is no CPU
+fallback: if the library is missing or fails to load, construction raises.
+Arrays may be NumPy arrays (host) or torch tensors (host or CUDA); results
+are written where the caller's buffers live.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libapf.so")
+
+APF_OK, APF_EINVAL, APF_ENOMEM, APF_ESINGULAR = 0, -1, -2, -3
+APF_ENOCONV, APF_ETIMEOUT, APF_ECUDA, APF_ESTATE = -4, -5, -6, -7
+APF_FP64, APF_MIXED_BF16X3 = 0, 1
+APF_OBJ_POWER, APF_OBJ_SPLITTER = 1, 2
+
+PRECISIONS = {"fp64": APF_FP64, "mixed": APF_MIXED_BF16X3, "bf16x3": APF_MIXED_BF16X3}
+OBJECTIVES = {"power": APF_OBJ_POWER, "splitter": APF_OBJ_SPLITTER}
+
+# Every symbol that include/apf.h declares.
+EXPORTS = ("apf_create", "apf_destroy", "apf_set_grid", "apf_set_eps", "apf_set_channels",
+           "apf_get_channels", "apf_solve_S", "apf_solve_S_grad", "apf_grad_from_gamma",
+           "apf_set_refinement", "apf_get_stats", "apf_last_error", "apf_version")
+
+
+class APFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"apf error {code}: {msg}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("refine_iters", ctypes.c_int), ("residual", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_boundary", ctypes.c_double),
+                ("ms_eliminate", ctypes.c_double), ("ms_fields", ctypes.c_double),
+                ("ms_readout", ctypes.c_double), ("ms_gradient", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong), ("workspace_bytes", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PML(ctypes.Structure):
+    _fields_ = [("R0", ctypes.c_double), ("power", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libapf.so not found at {path}; build it with "
+                           "`python -m paper_2306_09257_gb300.build`")
+    L = ctypes.CDLL(path)
+    vp, ip, dp, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.apf_create.argtypes = [ctypes.POINTER(vp), i, i]
+    L.apf_destroy.argtypes = [vp]
+    L.apf_destroy.restype = None
+    L.apf_set_grid.argtypes = [vp, i, i, i, i, d, ctypes.POINTER(PML)]
+    L.apf_set_eps.argtypes = [vp, dp, i, i, d, d]
+    L.apf_set_channels.argtypes = [vp, ip, i, ip, i]
+    L.apf_get_channels.argtypes = [vp, ip, ip, ip, ip]
+    L.apf_solve_S.argtypes = [vp, dp, vp]
+    L.apf_solve_S_grad.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), i, dp, ctypes.POINTER(ctypes.c_double), dp, vp]
+    L.apf_grad_from_gamma.argtypes = [vp, dp, dp, vp]
+    L.apf_set_refinement.argtypes = [vp, d, i]
+    L.apf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.apf_last_error.argtypes = [vp]
+    L.apf_last_error.restype = ctypes.c_char_p
+    L.apf_version.argtypes = []
+    _lib = L
+    return L
+
+
+def _ptr(a, dtype) -> int:
+    """Raw pointer of a contiguous NumPy array or torch tensor of `dtype`."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags.c_contiguous:
+            raise TypeError(f"need a C-contiguous {dtype} array")
+        return a.ctypes.data
+    import torch
+    tmap = {np.float64: torch.float64, np.complex128: torch.complex128}
+    if not isinstance(a, torch.Tensor) or a.dtype != tmap[np.dtype(dtype).type] or not a.is_contiguous():
+        raise TypeError(f"need a contiguous {dtype} array or tensor")
+    return a.data_ptr()
+
+
+def _stream_of(*arrays):
+    for a in arrays:
+        if a is not None and not isinstance(a, np.ndarray):
+            import torch
+            if isinstance(a, torch.Tensor) and a.is_cuda:
+                return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    return None
+
+
+class Solver:
+    """One APF context on one GPU."""
+
+    def __init__(self, device: int = 0, precision: str = "fp64"):
+        self._L = load_library()
+        self._h = ctypes.c_void_p()
+        rc = self._L.apf_create(ctypes.byref(self._h), int(device), PRECISIONS[precision])
+        if rc != APF_OK:
+            raise APFError(rc, self._L.apf_last_error(None).decode())
+        self.precision = precision
+        self.device = device
+        self.nx = self.h = None
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.apf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int, allow=()):
+        if rc != APF_OK and rc not in allow:
+            raise APFError(rc, self._L.apf_last_error(self._h).decode())
+        return rc
+
+    def set_grid(self, nx, ny, npml_bot, npml_top, lambda_px, R0=1e-8, power=3.0):
+        p = PML(R0, power)
+        self._check(self._L.apf_set_grid(self._h, nx, ny, npml_bot, npml_top, float(lambda_px), ctypes.byref(p)))
+        self.nx = nx
+
+    def set_eps(self, eps_slab, eps_sub: float, eps_clad: float, j0: int = -1):
+        h = int(eps_slab.shape[0])
+        if isinstance(eps_slab, np.ndarray):
+            eps_slab = np.ascontiguousarray(eps_slab, dtype=np.float64)
+        self._check(self._L.apf_set_eps(self._h, _ptr(eps_slab, np.float64), int(j0), h,
+                                        float(eps_sub), float(eps_clad)))
+        self.h = h
+
+    def set_channels(self, m_in: Optional[Sequence[int]] = None, m_out: Optional[Sequence[int]] = None):
+        def arr(v):
+            if v is None:
+                return None, 0
+            a = (ctypes.c_int * len(v))(*[int(x) for x in v])
+            return a, len(v)
+        ai, ni = arr(m_in)
+        ao, no = arr(m_out)
+        self._check(self._L.apf_set_channels(self._h, ai, ni, ao, no))
+
+    def channels(self):
+        ni, no = ctypes.c_int(), ctypes.c_int()
+        self._check(self._L.apf_get_channels(self._h, ctypes.byref(ni), ctypes.byref(no), None, None))
+        mi = (ctypes.c_int * ni.value)()
+        mo = (ctypes.c_int * no.value)()
+        self._check(self._L.apf_get_channels(self._h, None, None, mi, mo))
+        return np.array(mi[:], dtype=np.int64), np.array(mo[:], dtype=np.int64)
+
+    def set_refinement(self, tol: float, max_iters: int):
+        self._check(self._L.apf_set_refinement(self._h, float(tol), int(max_iters)))
+
+    def _alloc_S(self):
+        mi, mo = self.channels()
+        return np.empty((len(mo), len(mi)), dtype=np.complex128)
+
+    def solve_S(self, out=None, allow_noconv=False):
+        S = self._alloc_S() if out is None else out
+        st = _stream_of(S)
+        self._check(self._L.apf_solve_S(self._h, _ptr(S, np.complex128), st),
+                    allow=(APF_ENOCONV,) if allow_noconv else ())
+        return S
+
+    @staticmethod
+    def objective_params(kind: str, orders: Sequence[int], target: float = 0.0):
+        vals = [float(target), float(len(orders))] + [float(o) for o in orders]
+        return OBJECTIVES[kind], (ctypes.c_double * len(vals))(*vals), len(vals)
+
+    def solve_S_grad(self, kind: str, orders: Sequence[int], target: float = 0.0,
+                     out_S=None, out_grad=None, allow_noconv=False):
+        S = self._alloc_S() if out_S is None else out_S
+        g = np.empty((self.h, self.nx), dtype=np.float64) if out_grad is None else out_grad
+        oid, params, npar = self.objective_params(kind, orders, target)
+        f = ctypes.c_double()
+        st = _stream_of(S, g)
+        self._check(self._L.apf_solve_S_grad(self._h, oid, params, npar, _ptr(S, np.complex128),
+                                             ctypes.byref(f), _ptr(g, np.float64), st),
+                    allow=(APF_ENOCONV,) if allow_noconv else ())
+        return S, f.value, g
+
+    def grad_from_gamma(self, Gamma, out=None):
+        g = np.empty((self.h, self.nx), dtype=np.float64) if out is None else out
+        if isinstance(Gamma, np.ndarray):
+            Gamma = np.ascontiguousarray(Gamma, dtype=np.complex128)
+        st = _stream_of(Gamma, g)
+        self._check(self._L.apf_grad_from_gamma(self._h, _ptr(Gamma, np.complex128), _ptr(g, np.float64), st))
+        return g
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self._L.apf_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+
+def solver_for_workload(w, eps_slab, precision="fp64", device=0, m_in=None, m_out=None) -> Solver:
+    s = Solver(device=device, precision=precision)
+    s.set_grid(w.nx, w.ny, w.npml, w.npml, w.lambda_px)
+    s.set_eps(eps_slab, w.eps_sub, w.eps_clad, j0=w.j0)
+    s.set_channels(m_in, m_out)
+    return s

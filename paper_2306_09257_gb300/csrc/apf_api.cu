@@ -1,0 +1,444 @@
+// C ABI of libapf: argument checks, workspace, and the solve pipeline.
+//
+// One solve = (a2) per-mode boundary elimination -> (a3/a4) slab assembly and
+// block-Schur elimination -> (a5/a6) right-hand-side sweeps for the M_in
+// forward and M_out adjoint columns (+ refinement in mixed mode) -> (a7) S,
+// f, Gamma -> (a8) adjoint contraction.  These are the single-elimination
+// counterparts of the paper's APF with the augmented inputs B~ = [B, U] and
+// outputs C~ = [C; U^T] (Eq. 4): the slab fields F = (A^-1 B)|slab = U^T A^-1 B
+// and Phi = (A^-1 C^T)|slab = (C A^-1 U)^T are exactly the two blocks the
+// gradient needs, and U^T A^-1 U is never formed.
+#include "apf_internal.h"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+
+static std::string g_create_err = "no error";
+
+int set_err(apf_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_create_err = buf;
+    return code;
+}
+
+int check_cuda(apf_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return APF_OK;
+    cudaGetLastError();
+    return set_err(c, e == cudaErrorMemoryAllocation ? APF_ENOMEM : APF_ECUDA, "%s: %s", what,
+                   cudaGetErrorString(e));
+}
+
+GridDev make_grid(const apf_ctx *c) {
+    GridDev g;
+    g.nx = c->nx; g.ny = c->ny; g.npml_bot = c->npml_bot; g.npml_top = c->npml_top;
+    g.j0 = c->j0; g.h = c->h; g.jsrc = c->npml_bot; g.jout = c->ny - c->npml_top - 1;
+    g.k = c->k; g.eps_sub = c->eps_sub; g.eps_clad = c->eps_clad; g.R0 = c->R0; g.power = c->power;
+    return g;
+}
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static void free_workspace(apf_ctx *c) {
+    mixed_free(c);
+    for (void *p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    c->ws_bytes = 0;
+    c->ws_nx = c->ws_h = c->ws_min = c->ws_mout = -1;
+    c->d_min = c->d_mout = nullptr; c->d_modes = c->d_coef = c->d_circ = c->d_tw = nullptr;
+    c->d_G = c->d_scr1 = c->d_scr2 = c->d_E = c->d_T = c->d_R = nullptr;
+    c->d_S = c->d_Gam = c->d_Q = c->d_fft = nullptr;
+    c->d_grad = c->d_f = c->d_colnorm = nullptr;
+    c->d_flags = nullptr; c->d_pairs = nullptr;
+}
+
+template <typename T>
+static int dalloc(apf_ctx *c, T **p, size_t count) {
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, APF_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    c->ws_bytes += (long long)bytes;
+    *p = (T *)q;
+    return APF_OK;
+}
+
+// (Re)allocate the solve workspace when the problem size changed.  Solves never allocate.
+static int ensure_workspace(apf_ctx *c) {
+    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size();
+    if (c->ws_nx == c->nx && c->ws_h == c->h && c->ws_min == nin && c->ws_mout == nout) return APF_OK;
+    free_workspace(c);
+    long long nx = c->nx, h = c->h, ncol = nin + nout;
+    int rc;
+#define AL(p, n) if ((rc = dalloc(c, &(p), (size_t)(n))) != APF_OK) { free_workspace(c); return rc; }
+    AL(c->d_min, nin); AL(c->d_mout, nout);
+    AL(c->d_modes, 4 * nx); AL(c->d_coef, ncol); AL(c->d_circ, 2 * nx); AL(c->d_tw, nx / 2);
+    if (c->precision == APF_FP64) {
+        AL(c->d_G, h * nx * nx);
+        AL(c->d_scr1, nx * nx / 2); AL(c->d_scr2, nx * nx / 2);
+    }
+    AL(c->d_E, h * ncol * nx); AL(c->d_T, ncol * nx); AL(c->d_fft, ncol * nx);
+    if (c->precision != APF_FP64) { AL(c->d_R, h * ncol * nx); }
+    AL(c->d_S, (long long)nout * nin); AL(c->d_Gam, (long long)nout * nin);
+    AL(c->d_Q, h * nout * nx); AL(c->d_grad, h * nx);
+    AL(c->d_f, 8); AL(c->d_colnorm, 2 * ncol); AL(c->d_flags, 4);
+#undef AL
+    if (c->precision != APF_FP64) {
+        if ((rc = mixed_alloc(c)) != APF_OK) { free_workspace(c); return rc; }
+    }
+    cudaError_t e = cudaMemcpy(c->d_min, c->m_in.data(), sizeof(int) * nin, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_mout, c->m_out.data(), sizeof(int) * nout, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { free_workspace(c); return check_cuda(c, e, "upload channels"); }
+    launch_twiddles(c, 0);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { free_workspace(c); return check_cuda(c, e, "twiddles"); }
+    c->ws_nx = c->nx; c->ws_h = c->h; c->ws_min = nin; c->ws_mout = nout;
+    return APF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Channel selection: orders propagating in a uniform medium of the grid
+// (5-point dispersion sin^2(k_y/2) = k^2 eps/4 - sin^2(pi m/nx) in (0, 1)).
+// ---------------------------------------------------------------------------
+static double disp_q(const apf_ctx *c, int m, double eps) {
+    double s = sin(M_PI * (double)m / (double)c->nx);
+    return c->k * c->k * eps / 4.0 - s * s;
+}
+
+extern "C" {
+
+int apf_version(void) { return (1 << 16) | 0; }
+
+int apf_create(apf_ctx **out, int cuda_device, int precision) {
+    if (!out) return set_err(nullptr, APF_EINVAL, "apf_create: out is NULL");
+    *out = nullptr;
+    if (precision != APF_FP64 && precision != APF_MIXED_BF16X3)
+        return set_err(nullptr, APF_EINVAL, "apf_create: unknown precision %d", precision);
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return set_err(nullptr, APF_ECUDA, "apf_create: no CUDA device (%s)", cudaGetErrorString(e));
+    }
+    if (cuda_device < 0 || cuda_device >= ndev)
+        return set_err(nullptr, APF_EINVAL, "apf_create: device %d not in [0,%d)", cuda_device, ndev);
+    e = cudaSetDevice(cuda_device);
+    if (e != cudaSuccess) return set_err(nullptr, APF_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    if (precision == APF_MIXED_BF16X3) {
+        cudaDeviceProp p;
+        cudaGetDeviceProperties(&p, cuda_device);
+        if (p.major != 10 || p.minor != 3)
+            return set_err(nullptr, APF_EINVAL, "mixed mode needs an sm_103 GPU (found sm_%d%d)", p.major, p.minor);
+    }
+    apf_ctx *c = new apf_ctx();
+    c->device = cuda_device;
+    c->precision = precision;
+    for (auto &ev : c->ev) cudaEventCreate(&ev);
+    slab64_init_attrs();
+    mixed_init_attrs();
+    *out = c;
+    return APF_OK;
+}
+
+void apf_destroy(apf_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    free_workspace(c);
+    if (c->d_eps) cudaFree(c->d_eps);
+    for (auto &ev : c->ev) if (ev) cudaEventDestroy(ev);
+    delete c;
+}
+
+const char *apf_last_error(const apf_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+int apf_set_grid(apf_ctx *c, int nx, int ny, int npml_bot, int npml_top, double lambda_px,
+                 const apf_pml_params *pml) {
+    if (!c) return APF_EINVAL;
+    if (nx < 8 || nx > 8192 || (nx & (nx - 1)))
+        return set_err(c, APF_EINVAL, "nx=%d must be a power of two in [8, 8192]", nx);
+    if (npml_bot < 1 || npml_top < 1) return set_err(c, APF_EINVAL, "PML thickness must be >= 1");
+    if (ny < npml_bot + npml_top + 4) return set_err(c, APF_EINVAL, "ny=%d too small for the PMLs", ny);
+    if (!(lambda_px > 2.0) || !isfinite(lambda_px)) return set_err(c, APF_EINVAL, "lambda_px must be > 2");
+    double R0 = 1e-8, power = 3.0;
+    if (pml) { R0 = pml->R0; power = pml->power; }
+    if (!(R0 > 0.0 && R0 < 1.0) || !(power >= 0.0 && power <= 10.0))
+        return set_err(c, APF_EINVAL, "PML parameters out of range (0<R0<1, 0<=p<=10)");
+    c->nx = nx; c->ny = ny; c->npml_bot = npml_bot; c->npml_top = npml_top;
+    c->lambda_px = lambda_px; c->k = 2.0 * M_PI / lambda_px; c->R0 = R0; c->power = power;
+    c->grid_set = true;
+    c->eps_set = false;
+    c->ch_set = false;
+    return APF_OK;
+}
+
+int apf_set_eps(apf_ctx *c, const double *eps_slab, int j0, int h, double eps_sub, double eps_clad) {
+    if (!c) return APF_EINVAL;
+    if (!c->grid_set) return set_err(c, APF_ESTATE, "apf_set_eps before apf_set_grid");
+    if (!eps_slab) return set_err(c, APF_EINVAL, "eps_slab is NULL");
+    if (h < 1) return set_err(c, APF_EINVAL, "h=%d must be >= 1", h);
+    int jsrc = c->npml_bot, jout = c->ny - c->npml_top - 1;
+    if (j0 < 0) j0 = c->npml_bot + (c->ny - c->npml_bot - c->npml_top - h) / 2;
+    if (!(jsrc < j0 && j0 + h <= jout))
+        return set_err(c, APF_EINVAL, "slab rows [%d,%d) must lie strictly between source row %d and output row %d",
+                       j0, j0 + h, jsrc, jout);
+    if (!(eps_sub > 0.0) || !(eps_clad > 0.0) || !isfinite(eps_sub) || !isfinite(eps_clad))
+        return set_err(c, APF_EINVAL, "background permittivities must be positive and finite");
+    if (eps_clad > eps_sub) return set_err(c, APF_EINVAL, "eps_clad > eps_sub: cladding orders would not all propagate in the substrate");
+    cudaSetDevice(c->device);
+    long long n = (long long)h * c->nx;
+    if (c->h != h || !c->d_eps) {
+        if (c->d_eps) cudaFree(c->d_eps);
+        c->d_eps = nullptr;
+        cudaError_t e = cudaMalloc(&c->d_eps, sizeof(double) * n);
+        if (e != cudaSuccess) return check_cuda(c, e, "cudaMalloc eps");
+    }
+    if (is_device_ptr(eps_slab)) {
+        std::vector<double> tmp(n);
+        cudaError_t e = cudaMemcpy(tmp.data(), eps_slab, sizeof(double) * n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return check_cuda(c, e, "read eps");
+        for (long long i = 0; i < n; ++i)
+            if (!isfinite(tmp[i])) return set_err(c, APF_EINVAL, "eps_slab[%lld] is not finite", i);
+        e = cudaMemcpy(c->d_eps, eps_slab, sizeof(double) * n, cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) return check_cuda(c, e, "copy eps");
+    } else {
+        for (long long i = 0; i < n; ++i)
+            if (!isfinite(eps_slab[i])) return set_err(c, APF_EINVAL, "eps_slab[%lld] is not finite", i);
+        cudaError_t e = cudaMemcpy(c->d_eps, eps_slab, sizeof(double) * n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return check_cuda(c, e, "upload eps");
+    }
+    bool changed = (c->h != h) || (c->eps_sub != eps_sub) || (c->eps_clad != eps_clad);
+    c->h = h; c->j0 = j0; c->eps_sub = eps_sub; c->eps_clad = eps_clad;
+    c->eps_set = true;
+    if (changed) c->ch_set = false;
+    if (c->ch_set) return ensure_workspace(c);
+    return APF_OK;
+}
+
+int apf_set_channels(apf_ctx *c, const int *m_in, int n_in, const int *m_out, int n_out) {
+    if (!c) return APF_EINVAL;
+    if (!c->grid_set || !c->eps_set) return set_err(c, APF_ESTATE, "apf_set_channels needs grid and eps first");
+    std::vector<int> vin, vout, all;
+    for (int m = -(c->nx / 2); m < c->nx - c->nx / 2; ++m) {
+        double q = disp_q(c, m, c->eps_clad);
+        if (q > 0.0 && q < 1.0) all.push_back(m);
+    }
+    if (m_in && n_in > 0) vin.assign(m_in, m_in + n_in); else vin = all;
+    if (m_out && n_out > 0) vout.assign(m_out, m_out + n_out); else vout = all;
+    if (vin.empty() || vout.empty()) return set_err(c, APF_EINVAL, "no channels");
+    for (int m : vin) {
+        double q = disp_q(c, m, c->eps_sub);
+        if (!(q > 0.0 && q < 1.0)) return set_err(c, APF_EINVAL, "input order %d does not propagate in the substrate", m);
+    }
+    for (size_t i = 0; i < vout.size(); ++i) {
+        double q = disp_q(c, vout[i], c->eps_clad);
+        if (!(q > 0.0 && q < 1.0)) return set_err(c, APF_EINVAL, "output order %d does not propagate in the cladding", vout[i]);
+        if (i > 0 && vout[i] <= vout[i - 1]) return set_err(c, APF_EINVAL, "output orders must be strictly ascending");
+    }
+    c->m_in = vin;
+    c->m_out = vout;
+    c->ch_set = true;
+    cudaSetDevice(c->device);
+    int rc = ensure_workspace(c);
+    if (rc != APF_OK) { c->ch_set = false; return rc; }
+    // the orders may have changed with the same counts
+    cudaMemcpy(c->d_min, c->m_in.data(), sizeof(int) * c->m_in.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_mout, c->m_out.data(), sizeof(int) * c->m_out.size(), cudaMemcpyHostToDevice);
+    return APF_OK;
+}
+
+int apf_get_channels(const apf_ctx *c, int *n_in, int *n_out, int *m_in, int *m_out) {
+    if (!c) return APF_EINVAL;
+    if (!c->ch_set) return APF_ESTATE;
+    if (n_in) *n_in = (int)c->m_in.size();
+    if (n_out) *n_out = (int)c->m_out.size();
+    if (m_in) std::copy(c->m_in.begin(), c->m_in.end(), m_in);
+    if (m_out) std::copy(c->m_out.begin(), c->m_out.end(), m_out);
+    return APF_OK;
+}
+
+int apf_set_refinement(apf_ctx *c, double tol, int max_iters) {
+    if (!c) return APF_EINVAL;
+    if (!(tol > 0.0) || max_iters < 0 || max_iters > 100)
+        return set_err(c, APF_EINVAL, "refinement: tol > 0 and 0 <= max_iters <= 100");
+    c->ir_tol = tol;
+    c->ir_max = max_iters;
+    return APF_OK;
+}
+
+int apf_get_stats(const apf_ctx *c, apf_stats *st) {
+    if (!c || !st) return APF_EINVAL;
+    *st = c->stats;
+    st->workspace_bytes = c->ws_bytes;
+    return APF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Solve pipeline
+// ---------------------------------------------------------------------------
+static void fields64(apf_ctx *c, cudaStream_t s) {
+    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    long long nx = c->nx, L = (long long)ncol * nx, nn = nx * nx;
+    const double2 one = cmk(1, 0), zero = cmk(0, 0);
+    // forward chain Y_j = G_{j-1} Y_{j-1} (input columns; Y_0 = R_0)
+    for (int j = 1; j < c->h; ++j)
+        zgemm(c, false, false, nin, c->nx, c->nx, one, c->d_E + (j - 1) * L, nx, 0, c->d_G + (j - 1) * nn, nx, 0,
+              zero, c->d_E + j * L, nx, 0, 1, s);
+    // back substitution E_{h-1} = G_{h-1} Y_{h-1}; E_j = G_j (Y_j + E_{j+1})
+    for (int j = c->h - 1; j >= 0; --j) {
+        if (j == c->h - 1) launch_copy(c, c->d_T, c->d_E + j * L, L, s);
+        else launch_add(c, c->d_T, c->d_E + j * L, c->d_E + (j + 1) * L, L, s);
+        zgemm(c, false, false, ncol, c->nx, c->nx, one, c->d_T, nx, 0, c->d_G + j * nn, nx, 0, zero,
+              c->d_E + j * L, nx, 0, 1, s);
+    }
+}
+
+static int run_solve(apf_ctx *c, cudaStream_t s) {
+    if (!c->grid_set || !c->eps_set || !c->ch_set)
+        return set_err(c, APF_ESTATE, "solve needs apf_set_grid, apf_set_eps and apf_set_channels");
+    cudaSetDevice(c->device);
+    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    long long nx = c->nx, L = (long long)ncol * nx;
+    c->launches = 0;
+    c->stats.refine_iters = 0;
+    c->stats.residual = 0.0;
+    cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), s);
+    cudaEventRecord(c->ev[0], s);
+    launch_boundary(c, s);
+    cudaEventRecord(c->ev[1], s);
+    int rc = APF_OK;
+    if (c->precision == APF_FP64) {
+        long long nn = nx * nx;
+        for (int j = 0; j < c->h; ++j) {
+            double2 *X = c->d_G + j * nn;
+            launch_assemble64(c, j, X, j > 0 ? c->d_G + (j - 1) * nn : nullptr, s);
+            invert_sym64(c, X, c->nx, nx, c->d_scr1, c->d_scr2, s);
+        }
+    } else {
+        rc = mixed_eliminate(c, s);
+        if (rc != APF_OK) return rc;
+    }
+    cudaEventRecord(c->ev[2], s);
+    launch_zero(c, c->d_E, sizeof(double2) * c->h * L, s);
+    launch_build_rhs(c, c->d_E, s);
+    if (c->precision == APF_FP64) fields64(c, s);
+    else {
+        rc = mixed_solve_fields(c, s);
+        if (rc != APF_OK && rc != APF_ENOCONV) return rc;
+    }
+    cudaEventRecord(c->ev[3], s);
+    launch_readout(c, s);
+    cudaEventRecord(c->ev[4], s);
+    return rc;
+}
+
+static int finish(apf_ctx *c, cudaStream_t s, int rc_solve) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return check_cuda(c, e, "solve");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return check_cuda(c, e, "kernel launch");
+    int flags = 0;
+    cudaMemcpy(&flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost);
+    float ms[6] = {0};
+    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]);
+    c->stats.ms_boundary = ms[0];
+    c->stats.ms_eliminate = ms[1];
+    c->stats.ms_fields = ms[2];
+    c->stats.ms_readout = ms[3];
+    c->stats.ms_gradient = ms[4];
+    float tot = 0;
+    cudaEventElapsedTime(&tot, c->ev[0], c->ev[5]);
+    c->stats.ms_total = tot;
+    c->stats.kernel_launches = c->launches;
+    if (flags & FLAG_SINGULAR) return set_err(c, APF_ESINGULAR, "zero pivot in a diagonal-block inversion");
+    if (flags & FLAG_TIMEOUT) return set_err(c, APF_ETIMEOUT, "a bounded device wait gave up");
+    if (flags & FLAG_NONFINITE) return set_err(c, APF_ECUDA, "non-finite value in the elimination");
+    if (rc_solve == APF_ENOCONV)
+        return set_err(c, APF_ENOCONV, "refinement stopped at residual %.3e > tol %.3e", c->stats.residual, c->ir_tol);
+    return APF_OK;
+}
+
+extern "C" {
+
+int apf_solve_S(apf_ctx *c, double *S, void *stream) {
+    if (!c) return APF_EINVAL;
+    if (!S) return set_err(c, APF_EINVAL, "S is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = run_solve(c, s);
+    if (rc != APF_OK && rc != APF_ENOCONV) { cudaStreamSynchronize(s); return rc; }
+    cudaEventRecord(c->ev[5], s);
+    size_t bytes = sizeof(double2) * c->m_in.size() * c->m_out.size();
+    cudaMemcpyAsync(S, c->d_S, bytes, cudaMemcpyDefault, s);
+    return finish(c, s, rc);
+}
+
+int apf_solve_S_grad(apf_ctx *c, int objective, const double *params, int n_params, double *S, double *f,
+                     double *grad_eps, void *stream) {
+    if (!c) return APF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!grad_eps) return set_err(c, APF_EINVAL, "grad_eps is NULL");
+    if (!c->grid_set || !c->eps_set || !c->ch_set)
+        return set_err(c, APF_ESTATE, "solve needs apf_set_grid, apf_set_eps and apf_set_channels");
+    // validate objective params before any launch
+    if (objective != APF_OBJ_POWER && objective != APF_OBJ_SPLITTER)
+        return set_err(c, APF_EINVAL, "unknown objective id %d", objective);
+    if (!params || n_params < 2 || (int)params[1] < 1 || (int)params[1] > 16 || n_params != 2 + (int)params[1])
+        return set_err(c, APF_EINVAL, "objective params must be {t, nD, d_1..d_nD} with 1 <= nD <= 16");
+    int rc = run_solve(c, s);
+    if (rc != APF_OK && rc != APF_ENOCONV) { cudaStreamSynchronize(s); return rc; }
+    int rc2 = launch_objective(c, objective, params, n_params, s);
+    if (rc2 != APF_OK) { cudaStreamSynchronize(s); return rc2; }
+    launch_gradient(c, c->d_Gam, s);
+    cudaEventRecord(c->ev[5], s);
+    size_t sb = sizeof(double2) * c->m_in.size() * c->m_out.size();
+    if (S) cudaMemcpyAsync(S, c->d_S, sb, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(grad_eps, c->d_grad, sizeof(double) * c->h * c->nx, cudaMemcpyDefault, s);
+    double fh = 0.0;
+    cudaMemcpyAsync(&fh, c->d_f, sizeof(double), cudaMemcpyDeviceToHost, s);
+    int r = finish(c, s, rc);
+    if (f) *f = fh;
+    return r;
+}
+
+int apf_grad_from_gamma(apf_ctx *c, const double *Gamma, double *grad_eps, void *stream) {
+    if (!c) return APF_EINVAL;
+    if (!Gamma || !grad_eps) return set_err(c, APF_EINVAL, "Gamma / grad_eps is NULL");
+    if (!c->ch_set || c->ws_nx < 0) return set_err(c, APF_ESTATE, "apf_grad_from_gamma needs a previous solve");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaSetDevice(c->device);
+    size_t sb = sizeof(double2) * c->m_in.size() * c->m_out.size();
+    cudaMemcpyAsync(c->d_Gam, Gamma, sb, cudaMemcpyDefault, s);
+    c->launches = 0;
+    cudaEventRecord(c->ev[4], s);
+    launch_gradient(c, c->d_Gam, s);
+    cudaEventRecord(c->ev[5], s);
+    cudaMemcpyAsync(grad_eps, c->d_grad, sizeof(double) * c->h * c->nx, cudaMemcpyDefault, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return check_cuda(c, e, "grad_from_gamma");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
+    c->stats.ms_gradient = ms;
+    return APF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// Internal declarations shared by the CUDA translation units of libapf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/apf.h"
+
+// ---------------------------------------------------------------------------
+// complex float64 helpers (interleaved double2)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double2 cmk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    // Smith's algorithm (avoids overflow for large |b|).
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        double r = b.x / b.y, d = b.y + b.x * r;
+        return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
+__host__ __device__ __forceinline__ double2 cinv(double2 b) { return cdiv(make_double2(1.0, 0.0), b); }
+
+// complex float32 helpers
+__host__ __device__ __forceinline__ float2 fmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// ---------------------------------------------------------------------------
+// Grid description passed by value to kernels.
+// ---------------------------------------------------------------------------
+struct GridDev {
+    int nx, ny, npml_bot, npml_top;
+    int j0, h, jsrc, jout;
+    double k;            // 2 pi / lambda_px
+    double eps_sub, eps_clad;
+    double R0, power;
+};
+
+// Error flag bits written by kernels into ctx->d_flags[0].
+enum { FLAG_SINGULAR = 1, FLAG_NONFINITE = 2, FLAG_TIMEOUT = 4 };
+
+// Sizes of the mixed-mode (tensor-core) workspace; defined in tc_gemm.cu.
+struct MixedWork;
+
+struct apf_ctx {
+    int device = 0;
+    int precision = APF_FP64;
+    // grid
+    bool grid_set = false;
+    int nx = 0, ny = 0, npml_bot = 0, npml_top = 0;
+    double lambda_px = 0, k = 0, R0 = 1e-8, power = 3.0;
+    // slab
+    bool eps_set = false;
+    int h = 0, j0 = 0;
+    double eps_sub = 1, eps_clad = 1;
+    // channels
+    bool ch_set = false;
+    std::vector<int> m_in, m_out;
+    // refinement
+    double ir_tol = 1e-10;
+    int ir_max = 8;
+    // workspace signature
+    int ws_nx = -1, ws_h = -1, ws_min = -1, ws_mout = -1;
+    long long ws_bytes = 0;
+    std::vector<void *> allocs;
+    // device buffers (float64 path, also used by the mixed path)
+    double *d_eps = nullptr;     // h*nx
+    int *d_min = nullptr, *d_mout = nullptr;
+    double2 *d_modes = nullptr;  // 4*nx: sigma_bot, sigma_top, fac_bot, tau
+    double2 *d_coef = nullptr;   // n_in + n_out: beta_a, w_b
+    double2 *d_circ = nullptr;   // 2*nx: circulant generators of Sigma_bot, Sigma_top
+    double2 *d_tw = nullptr;     // nx/2 twiddles exp(-2 pi i k / nx)
+    double2 *d_G = nullptr;      // h*nx*nx   (float64 mode)
+    double2 *d_scr1 = nullptr, *d_scr2 = nullptr;  // recursion scratch, nx*nx/2 each
+    double2 *d_E = nullptr;      // h*ncol*nx fields, [row][column][x]
+    double2 *d_T = nullptr;      // ncol*nx temp
+    double2 *d_R = nullptr;      // h*ncol*nx residual (mixed)
+    double2 *d_S = nullptr, *d_Gam = nullptr;  // n_out*n_in
+    double2 *d_Q = nullptr;      // h*n_out*nx
+    double2 *d_fft = nullptr;    // ncol*nx
+    double *d_grad = nullptr;    // h*nx
+    double *d_f = nullptr;       // scalars: f, residual norms
+    double *d_colnorm = nullptr; // 2*ncol: ||R||, ||r|| per column
+    int *d_flags = nullptr;
+    int *d_pairs = nullptr;      // objective (b, a) pairs
+    MixedWork *mw = nullptr;
+    // stats
+    apf_stats stats{};
+    long long launches = 0;
+    cudaEvent_t ev[8] = {};
+    std::string err;
+};
+
+// ---------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------
+#define APF_LAUNCH(ctx, kernel, grid, block, smem, stream, ...)              \
+    do {                                                                      \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);           \
+        (ctx)->launches++;                                                    \
+    } while (0)
+
+GridDev make_grid(const apf_ctx *c);
+
+// boundary.cu
+void launch_boundary(apf_ctx *c, cudaStream_t s);
+void launch_build_rhs(apf_ctx *c, double2 *E, cudaStream_t s);
+void launch_twiddles(apf_ctx *c, cudaStream_t s);
+void launch_fft(apf_ctx *c, const double2 *in, double2 *out, int n, int batch, long long in_stride,
+                long long out_stride, int sign, double scale, cudaStream_t s);
+int fft_smem_bytes(int n);
+
+// slab64.cu
+void launch_assemble64(apf_ctx *c, int row, double2 *X, const double2 *Gprev, cudaStream_t s);
+void zgemm(apf_ctx *c, bool ta, bool tb, int M, int N, int K, double2 alpha,
+           const double2 *A, long long lda, long long sA,
+           const double2 *B, long long ldb, long long sB, double2 beta,
+           double2 *C, long long ldc, long long sC, int batch, cudaStream_t s);
+void invert_sym64(apf_ctx *c, double2 *X, int n, long long ld, double2 *scr1, double2 *scr2, cudaStream_t s);
+void launch_add(apf_ctx *c, double2 *T, const double2 *a, const double2 *b, long long n, cudaStream_t s);
+void launch_copy(apf_ctx *c, double2 *dst, const double2 *src, long long n, cudaStream_t s);
+void launch_zero(apf_ctx *c, void *dst, long long bytes, cudaStream_t s);
+
+// readout.cu
+void launch_readout(apf_ctx *c, cudaStream_t s);  // S from fields
+int launch_objective(apf_ctx *c, int objective, const double *params, int n_params, cudaStream_t s);
+void launch_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s);
+
+// residual.cu
+void launch_residual(apf_ctx *c, const double2 *E, double2 *r, cudaStream_t s);
+void launch_colnorms(apf_ctx *c, const double2 *X, double *out, int ncol, cudaStream_t s);
+void launch_axpy_fields(apf_ctx *c, double2 *E, const double2 *d, long long n, cudaStream_t s);
+
+// mixed.cu
+int mixed_alloc(apf_ctx *c);
+void mixed_free(apf_ctx *c);
+int mixed_eliminate(apf_ctx *c, cudaStream_t s);
+int mixed_solve_fields(apf_ctx *c, cudaStream_t s);
+
+int set_err(apf_ctx *c, int code, const char *fmt, ...);
+void slab64_init_attrs();
+void mixed_init_attrs();
+int check_cuda(apf_ctx *c, cudaError_t e, const char *what);

@@ -1,0 +1,202 @@
+// Per-Fourier-mode boundary elimination, channel coefficients, right-hand
+// sides, and a float64 FFT.
+//
+// Rows outside the design slab have x-uniform permittivity, so in the Fourier
+// basis u_m(x) = exp(2 pi i m x/nx)/sqrt(nx) every such row of A is diagonal:
+// for order m the block-tridiagonal A restricted to those rows is a scalar
+// tridiagonal recurrence along y.  Eliminating the substrate + bottom PML
+// (from the bottom wall up) and the cladding + top PML (from the top wall
+// down) leaves, on the first and last slab rows, diagonal (in m) Schur terms
+// sigma_bot[m], sigma_top[m]; the input source row's coefficient reaches the
+// first slab row multiplied by fac_bot[m]; and the field on the last slab row
+// reaches the output row multiplied by tau[m].  This is the structured
+// replacement of the sparse partial factorization of K = [A, B; C, D]
+// (paper Sec. 2, first paragraph): S = C A^-1 B without assembling A.
+#include "apf_internal.h"
+
+#include <math.h>
+
+namespace {
+
+__device__ double2 stretch_at(const GridDev &g, double y) {
+    double lo = g.npml_bot - 0.5, hi = g.ny - g.npml_top - 0.5;
+    double L, d, eps;
+    if (y < lo) {
+        L = g.npml_bot; d = lo - y; eps = g.eps_sub;
+    } else if (y > hi) {
+        L = g.npml_top; d = y - hi; eps = g.eps_clad;
+    } else {
+        return cmk(1.0, 0.0);
+    }
+    double alpha = -(g.power + 1.0) * log(g.R0) / (2.0 * g.k * sqrt(eps) * L);
+    return cmk(1.0, alpha * pow(d / L, g.power));
+}
+
+// Diagonal of row j for Fourier order with eigenvalue lam of -d2/dx2:
+// s_j (lam - k^2 eps) + 1/s_{j+1/2} + 1/s_{j-1/2}.
+__device__ double2 row_diag(const GridDev &g, int j, double lam, double eps) {
+    double2 s = stretch_at(g, (double)j);
+    double2 t = cscale(s, lam - g.k * g.k * eps);
+    t = cadd(t, cinv(stretch_at(g, j + 0.5)));
+    t = cadd(t, cinv(stretch_at(g, j - 0.5)));
+    return t;
+}
+
+__global__ void k_boundary_sweep(GridDev g, double2 *modes) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= g.nx) return;
+    double sp = sinpi((double)m / (double)g.nx);
+    double lam = 4.0 * sp * sp;
+    // bottom: substrate + PML, rows 0 .. j0-1, eliminated upward
+    double2 dt = row_diag(g, 0, lam, g.eps_sub);
+    double2 fac = cmk(1.0, 0.0);
+    for (int j = 1; j < g.j0; ++j) {
+        double2 c = cinv(stretch_at(g, j - 0.5));
+        if (j - 1 >= g.jsrc) fac = cmul(fac, cdiv(c, dt));
+        dt = csub(row_diag(g, j, lam, g.eps_sub), cdiv(cmul(c, c), dt));
+    }
+    double2 c0 = cinv(stretch_at(g, g.j0 - 0.5));
+    fac = cmul(fac, cdiv(c0, dt));
+    double2 sig_bot = cscale(cdiv(cmul(c0, c0), dt), -1.0);
+    // top: cladding + PML, rows ny-1 .. j0+h, eliminated downward
+    double2 dd = row_diag(g, g.ny - 1, lam, g.eps_clad);
+    double2 tau = cmk(1.0, 0.0);
+    for (int j = g.ny - 2; j >= g.j0 + g.h; --j) {
+        double2 c = cinv(stretch_at(g, j + 0.5));
+        dd = csub(row_diag(g, j, lam, g.eps_clad), cdiv(cmul(c, c), dd));
+        if (j <= g.jout) tau = cmul(tau, cdiv(cinv(stretch_at(g, j - 0.5)), dd));
+    }
+    double2 c1 = cinv(stretch_at(g, g.j0 + g.h - 0.5));
+    double2 sig_top = cscale(cdiv(cmul(c1, c1), dd), -1.0);
+    modes[m] = sig_bot;
+    modes[g.nx + m] = sig_top;
+    modes[2 * g.nx + m] = fac;
+    modes[3 * g.nx + m] = tau;
+}
+
+// nu = sin(k_y) with sin^2(k_y/2) = k^2 eps/4 - sin^2(pi m/nx).
+__device__ double nu_of(const GridDev &g, int m, double eps) {
+    double sp = sinpi((double)m / (double)g.nx);
+    double q = g.k * g.k * eps * 0.25 - sp * sp;
+    double ky = 2.0 * asin(sqrt(q));
+    return sin(ky);
+}
+
+__device__ __forceinline__ int mod_nx(int m, int nx) { int r = m % nx; return r < 0 ? r + nx : r; }
+
+__global__ void k_channel_coef(GridDev g, const int *m_in, int n_in, const int *m_out, int n_out,
+                               const double2 *modes, double2 *coef) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n_in) {
+        int m = m_in[c];
+        double nu = nu_of(g, m, g.eps_sub);
+        // source -2i sqrt(nu) carried to the first slab row
+        double2 b = cmk(0.0, -2.0 * sqrt(nu));
+        coef[c] = cmul(b, modes[2 * g.nx + mod_nx(m, g.nx)]);
+    } else if (c < n_in + n_out) {
+        int m = m_out[c - n_in];
+        double nu = nu_of(g, m, g.eps_clad);
+        coef[c] = cscale(modes[3 * g.nx + mod_nx(m, g.nx)], sqrt(nu));
+    }
+}
+
+// Right-hand sides of the slab system (rows [row][col][x]):
+// forward column a on the first slab row: beta_a u_{m_a}(x);
+// adjoint column n_in+b on the last slab row: w_b u_{-m_b}(x)
+// (C^T projected through the cladding; A = A^T).
+__global__ void k_build_rhs(GridDev g, const int *m_in, int n_in, const int *m_out, int n_out,
+                            const double2 *coef, double2 *E) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (x >= g.nx) return;
+    int ncol = n_in + n_out;
+    int row, m;
+    if (c < n_in) { row = 0; m = m_in[c]; }
+    else { row = g.h - 1; m = -m_out[c - n_in]; }
+    long long t = ((long long)mod_nx(m, g.nx) * x) % g.nx;
+    double sn, cs;
+    sincospi(2.0 * (double)t / (double)g.nx, &sn, &cs);
+    double inv = rsqrt((double)g.nx);
+    double2 v = cmul(coef[c], cmk(cs * inv, sn * inv));
+    E[((long long)row * ncol + c) * g.nx + x] = v;
+}
+
+__global__ void k_twiddles(double2 *tw, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n / 2) return;
+    double sn, cs;
+    sincospi(-2.0 * (double)i / (double)n, &sn, &cs);
+    tw[i] = cmk(cs, sn);
+}
+
+// Radix-2 decimation-in-time FFT of one length-n column per block, in shared
+// memory: out[k] = scale * sum_x in[x] exp(sign * 2 pi i k x / n).
+__global__ void k_fft(const double2 *in, double2 *out, int n, int logn, long long in_stride,
+                      long long out_stride, int sign, double scale, const double2 *tw) {
+    extern __shared__ double2 a[];
+    const double2 *src = in + (long long)blockIdx.x * in_stride;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        unsigned r = __brev((unsigned)i) >> (32 - logn);
+        a[r] = src[i];
+    }
+    __syncthreads();
+    for (int lh = 0; lh < logn; ++lh) {
+        int half = 1 << lh;
+        int tstride = n >> (lh + 1);
+        for (int t = threadIdx.x; t < n / 2; t += blockDim.x) {
+            int pos = t & (half - 1);
+            int i = ((t >> lh) << (lh + 1)) + pos;
+            int j = i + half;
+            double2 w = tw[pos * tstride];
+            if (sign > 0) w.y = -w.y;
+            double2 u = a[i];
+            double2 v = cmul(a[j], w);
+            a[i] = cadd(u, v);
+            a[j] = csub(u, v);
+        }
+        __syncthreads();
+    }
+    double2 *dst = out + (long long)blockIdx.x * out_stride;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = cscale(a[i], scale);
+}
+
+}  // namespace
+
+int fft_smem_bytes(int n) { return n * (int)sizeof(double2); }
+
+void launch_twiddles(apf_ctx *c, cudaStream_t s) {
+    int n = c->nx;
+    APF_LAUNCH(c, k_twiddles, (n / 2 + 255) / 256, 256, 0, s, c->d_tw, n);
+}
+
+void launch_fft(apf_ctx *c, const double2 *in, double2 *out, int n, int batch, long long in_stride,
+                long long out_stride, int sign, double scale, cudaStream_t s) {
+    if (batch <= 0) return;
+    int logn = 0;
+    while ((1 << logn) < n) ++logn;
+    int smem = fft_smem_bytes(n);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * (int)sizeof(double2));
+        attr_set = true;
+    }
+    int threads = n / 2 < 256 ? n / 2 : 256;
+    APF_LAUNCH(c, k_fft, batch, threads, smem, s, in, out, n, logn, in_stride, out_stride, sign, scale, c->d_tw);
+}
+
+void launch_boundary(apf_ctx *c, cudaStream_t s) {
+    GridDev g = make_grid(c);
+    APF_LAUNCH(c, k_boundary_sweep, (c->nx + 127) / 128, 128, 0, s, g, c->d_modes);
+    int nc = (int)(c->m_in.size() + c->m_out.size());
+    APF_LAUNCH(c, k_channel_coef, (nc + 127) / 128, 128, 0, s, g, c->d_min, (int)c->m_in.size(), c->d_mout,
+               (int)c->m_out.size(), c->d_modes, c->d_coef);
+    // circulant generators: c(d) = (1/nx) sum_m sigma_m exp(2 pi i m d / nx)
+    launch_fft(c, c->d_modes, c->d_circ, c->nx, 2, c->nx, c->nx, +1, 1.0 / c->nx, s);
+}
+
+void launch_build_rhs(apf_ctx *c, double2 *E, cudaStream_t s) {
+    GridDev g = make_grid(c);
+    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size();
+    dim3 grid((c->nx + 255) / 256, nin + nout);
+    APF_LAUNCH(c, k_build_rhs, grid, 256, 0, s, g, c->d_min, nin, c->d_mout, nout, c->d_coef, E);
+}

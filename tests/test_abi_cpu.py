@@ -1,0 +1,57 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol that include/apf.h declares, and refuses to run without a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2306_09257_gb300 import apf, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build_lib()
+    return apf.load_library()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "apf.h")).read()
+    return sorted(set(re.findall(r"\b(apf_[A-Za-z_]+)\s*\(", src)))
+
+
+def test_header_matches_binding_list():
+    assert declared_symbols() == sorted(apf.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_version(lib):
+    assert lib.apf_version() >> 16 == 1
+
+
+def test_create_without_device_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = lib.apf_create(ctypes.byref(h), 0, apf.APF_FP64)
+    assert rc == apf.APF_ECUDA
+    assert h.value is None
+    assert b"device" in lib.apf_last_error(None)
+
+
+def test_create_rejects_bad_precision(lib):
+    h = ctypes.c_void_p()
+    assert lib.apf_create(ctypes.byref(h), 0, 77) == apf.APF_EINVAL
+
+
+def test_null_context_calls(lib):
+    assert lib.apf_set_grid(None, 64, 100, 20, 20, 16.0, None) == apf.APF_EINVAL
+    assert lib.apf_solve_S(None, None, None) == apf.APF_EINVAL
+    lib.apf_destroy(None)
