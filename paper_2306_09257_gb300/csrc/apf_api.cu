@@ -408,7 +408,8 @@ int apf_solve_S_grad(apf_ctx *c, int objective, const double *params, int n_para
     if (rc != APF_OK && rc != APF_ENOCONV) { cudaStreamSynchronize(s); return rc; }
     int rc2 = launch_objective(c, objective, params, n_params, s);
     if (rc2 != APF_OK) { cudaStreamSynchronize(s); return rc2; }
-    launch_gradient(c, c->d_Gam, s);
+    rc2 = launch_gradient(c, c->d_Gam, s);
+    if (rc2 != APF_OK) { cudaStreamSynchronize(s); return rc2; }
     cudaEventRecord(c->ev[5], s);
     size_t sb = sizeof(double2) * c->m_in.size() * c->m_out.size();
     if (S) cudaMemcpyAsync(S, c->d_S, sb, cudaMemcpyDefault, s);
@@ -430,7 +431,8 @@ int apf_grad_from_gamma(apf_ctx *c, const double *Gamma, double *grad_eps, void 
     cudaMemcpyAsync(c->d_Gam, Gamma, sb, cudaMemcpyDefault, s);
     c->launches = 0;
     cudaEventRecord(c->ev[4], s);
-    launch_gradient(c, c->d_Gam, s);
+    int rc = launch_gradient(c, c->d_Gam, s);
+    if (rc != APF_OK) { cudaStreamSynchronize(s); return rc; }
     cudaEventRecord(c->ev[5], s);
     cudaMemcpyAsync(grad_eps, c->d_grad, sizeof(double) * c->h * c->nx, cudaMemcpyDefault, s);
     cudaError_t e = cudaStreamSynchronize(s);

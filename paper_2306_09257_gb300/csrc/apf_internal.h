@@ -137,12 +137,8 @@ void launch_zero(apf_ctx *c, void *dst, long long bytes, cudaStream_t s);
 // readout.cu
 void launch_readout(apf_ctx *c, cudaStream_t s);  // S from fields
 int launch_objective(apf_ctx *c, int objective, const double *params, int n_params, cudaStream_t s);
-void launch_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s);
-
-// residual.cu
-void launch_residual(apf_ctx *c, const double2 *E, double2 *r, cudaStream_t s);
-void launch_colnorms(apf_ctx *c, const double2 *X, double *out, int ncol, cudaStream_t s);
-void launch_axpy_fields(apf_ctx *c, double2 *E, const double2 *d, long long n, cudaStream_t s);
+int launch_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s);
+int mixed_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s);
 
 // mixed.cu
 int mixed_alloc(apf_ctx *c);

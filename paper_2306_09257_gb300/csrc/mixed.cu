@@ -1,10 +1,698 @@
-// Mixed-precision slab elimination (tensor cores); filled in by tc_gemm.cu.
+// Mixed-precision slab elimination and float64 iterative refinement.
+//
+// The slab Schur blocks X_j and their inverses G_j are held in float32
+// (separate real / imaginary planes).  Every product runs on the tensor cores
+// (tc_gemm.cu) with operands split into bf16 planes: two planes and three
+// products ("bf16x3") for the elimination and the field sweeps, three planes
+// and six products for the gradient contraction.  Accuracy is then won back
+// by float64 iterative refinement of the slab fields:
+//     r = R - K E (float64 5-point stencil + boundary circulants),
+//     E <- E + Khat^-1 r,
+// where Khat^-1 is the block-LU solve with the stored low-precision G_j.
 #include "apf_internal.h"
+#include "tc_gemm.h"
 
-struct MixedWork {};
+#include <algorithm>
+#include <vector>
 
-int mixed_alloc(apf_ctx *c) { return set_err(c, APF_EINVAL, "mixed precision is not available in this build"); }
-void mixed_free(apf_ctx *c) { (void)c; }
-int mixed_eliminate(apf_ctx *c, cudaStream_t) { return set_err(c, APF_EINVAL, "mixed precision is not available"); }
-int mixed_solve_fields(apf_ctx *c, cudaStream_t) { return set_err(c, APF_EINVAL, "mixed precision is not available"); }
-void mixed_init_attrs() {}
+struct MixedWork {
+    int nsplit_elim = 2, nsplit_grad = 3, leaf = 128;
+    float *Xre = nullptr, *Xim = nullptr;            // n x n working block
+    float *Tre = nullptr, *Tim = nullptr;            // recursion scratch (n*n/2 each)
+    float *Vre = nullptr, *Vim = nullptr;
+    __nv_bfloat16 *PA = nullptr, *PB = nullptr;      // operand packs
+    long long pa_elems = 0, pb_elems = 0;
+    __nv_bfloat16 *GP = nullptr;                     // packed G_j, h of them
+    long long gp_stride = 0;
+    float *O32 = nullptr;                            // GEMM output planes, 2 * max(ncol, n_out) * nx
+    double2 *r = nullptr, *delta = nullptr;          // refinement buffers (h*ncol*nx)
+    double2 *cb = nullptr, *ct = nullptr;            // circulant products on the boundary rows
+    double *rnorm = nullptr;                         // ||R_c||^2, ||r_c||^2
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+__device__ __forceinline__ void split_bf16(float x, int nsplit, __nv_bfloat16 *o) {
+    __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+    o[0] = h0;
+    if (nsplit > 1) {
+        float x1 = x - __bfloat162float(h0);
+        __nv_bfloat16 h1 = __float2bfloat16_rn(x1);
+        o[1] = h1;
+        if (nsplit > 2) o[2] = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+    }
+}
+
+// Pack a complex float32 planar matrix into bf16 split planes.
+// Logical element v(r, k) = trans ? src[k][r] : src[r][k], r < R, k < K.
+// layoutB = 0 (A operand): row r = [Re v(r,:), Im v(r,:)].
+// layoutB = 1 (B operand of C = A B, r indexing C's columns):
+//   row r = [Re v(r,:), -Im v(r,:)], row R + r = [Im v(r,:), Re v(r,:)].
+__global__ void k_pack32(const float *__restrict__ sre, const float *__restrict__ sim, long long ld, int R, int K,
+                         int trans, int layoutB, int nsplit, __nv_bfloat16 *out, long long kp,
+                         long long plane_pitch) {
+    __shared__ float tre[32][33], tim[32][33];
+    int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    int tx = threadIdx.x, ty = threadIdx.y;
+    for (int i = ty; i < 32; i += 8) {
+        if (!trans) {
+            int r = r0 + i, k = k0 + tx;
+            float a = 0.f, b = 0.f;
+            if (r < R && k < K) { a = sre[(long long)r * ld + k]; b = sim[(long long)r * ld + k]; }
+            tre[i][tx] = a; tim[i][tx] = b;
+        } else {
+            int k = k0 + i, r = r0 + tx;
+            float a = 0.f, b = 0.f;
+            if (r < R && k < K) { a = sre[(long long)k * ld + r]; b = sim[(long long)k * ld + r]; }
+            tre[tx][i] = a; tim[tx][i] = b;
+        }
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        int r = r0 + i, k = k0 + tx;
+        if (r >= R || k >= K) continue;
+        float a = tre[i][tx], b = tim[i][tx];
+        __nv_bfloat16 sa[3], sb[3], nb[3];
+        split_bf16(a, nsplit, sa);
+        split_bf16(b, nsplit, sb);
+        for (int p = 0; p < nsplit; ++p) nb[p] = __hneg(sb[p]);
+        for (int p = 0; p < nsplit; ++p) {
+            __nv_bfloat16 *o = out + p * plane_pitch;
+            if (!layoutB) {
+                o[(long long)r * kp + k] = sa[p];
+                o[(long long)r * kp + K + k] = sb[p];
+            } else {
+                o[(long long)r * kp + k] = sa[p];
+                o[(long long)r * kp + K + k] = nb[p];
+                o[(long long)(R + r) * kp + k] = sb[p];
+                o[(long long)(R + r) * kp + K + k] = sa[p];
+            }
+        }
+    }
+}
+
+// A-layout pack of complex float64 rows (optionally the sum of two sources):
+// row r = [Re v(r,:), Im v(r,:)], v = s1 (+ s2).
+__global__ void k_pack64_A(const double2 *__restrict__ s1, const double2 *__restrict__ s2, long long ld, int R,
+                           int K, int nsplit, __nv_bfloat16 *out, long long kp, long long plane_pitch) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int r = blockIdx.y;
+    if (k >= K || r >= R) return;
+    double2 v = s1[(long long)r * ld + k];
+    if (s2) v = cadd(v, s2[(long long)r * ld + k]);
+    __nv_bfloat16 sa[3], sb[3];
+    split_bf16((float)v.x, nsplit, sa);
+    split_bf16((float)v.y, nsplit, sb);
+    for (int p = 0; p < nsplit; ++p) {
+        __nv_bfloat16 *o = out + p * plane_pitch + (long long)r * kp;
+        o[k] = sa[p];
+        o[K + k] = sb[p];
+    }
+}
+
+// B-layout pack of the transpose of complex float64 rows: logical
+// v(r, k) = src[k][r] (r < R, k < K) -> rows r and R + r.
+__global__ void k_pack64_BT(const double2 *__restrict__ src, long long ld, int R, int K, int nsplit,
+                            __nv_bfloat16 *out, long long kp, long long plane_pitch) {
+    __shared__ double2 t[32][33];
+    int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    int tx = threadIdx.x, ty = threadIdx.y;
+    for (int i = ty; i < 32; i += 8) {
+        int k = k0 + i, r = r0 + tx;
+        double2 v = cmk(0, 0);
+        if (r < R && k < K) v = src[(long long)k * ld + r];
+        t[tx][i] = v;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        int r = r0 + i, k = k0 + tx;
+        if (r >= R || k >= K) continue;
+        double2 v = t[i][tx];
+        __nv_bfloat16 sa[3], sb[3];
+        split_bf16((float)v.x, nsplit, sa);
+        split_bf16((float)v.y, nsplit, sb);
+        for (int p = 0; p < nsplit; ++p) {
+            __nv_bfloat16 *o = out + p * plane_pitch;
+            o[(long long)r * kp + k] = sa[p];
+            o[(long long)r * kp + K + k] = __hneg(sb[p]);
+            o[(long long)(R + r) * kp + k] = sb[p];
+            o[(long long)(R + r) * kp + K + k] = sa[p];
+        }
+    }
+}
+
+// X_j = K_j - G_{j-1} in float32 planes (K_j: 5-point slab block plus the
+// boundary circulants on the first / last slab row).
+__global__ void k_assemble32(GridDev g, int row, const double *eps, const double2 *circ, const float *Gre,
+                             const float *Gim, float *Xre, float *Xim) {
+    int xp = blockIdx.x * blockDim.x + threadIdx.x;
+    int x = blockIdx.y;
+    int n = g.nx;
+    if (xp >= n) return;
+    double vr = 0.0, vi = 0.0;
+    if (xp == x) vr += 4.0 - g.k * g.k * eps[(long long)row * n + x];
+    if (xp == (x + 1) % n) vr -= 1.0;
+    if (xp == (x + n - 1) % n) vr -= 1.0;
+    int d = (x - xp + n) % n;
+    if (row == 0) { vr += circ[d].x; vi += circ[d].y; }
+    if (row == g.h - 1) { vr += circ[n + d].x; vi += circ[n + d].y; }
+    long long idx = (long long)x * n + xp;
+    float fr = (float)vr, fi = (float)vi;
+    if (Gre) { fr -= Gre[idx]; fi -= Gim[idx]; }
+    Xre[idx] = fr;
+    Xim[idx] = fi;
+}
+
+// Float32 Gauss-Jordan inverse of an n x n (n <= 128) diagonal block with
+// partial pivoting, in shared memory (planar in global memory).
+__global__ void __launch_bounds__(512) k_leaf_inv32(float *re, float *im, long long ld, int n, int *flags) {
+    extern __shared__ float2 a32[];
+    __shared__ float2 colk[128];
+    __shared__ int piv[128];
+    __shared__ int s_p;
+    __shared__ float2 s_inv;
+    int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < n * n; e += nt) {
+        long long gidx = (long long)(e / n) * ld + (e % n);
+        a32[e] = make_float2(re[gidx], im[gidx]);
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (tid < 32) {
+            float best = -1.f;
+            int bi = k;
+            for (int i = k + tid; i < n; i += 32) {
+                float2 v = a32[i * n + k];
+                float m = v.x * v.x + v.y * v.y;
+                if (m > best) { best = m; bi = i; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                float ob = __shfl_down_sync(0xffffffffu, best, off);
+                int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (tid == 0) {
+                s_p = bi;
+                piv[k] = bi;
+                if (!(best > 0.f) || !isfinite(best)) atomicOr(flags, FLAG_SINGULAR);
+            }
+        }
+        __syncthreads();
+        int p = s_p;
+        if (p != k) {
+            for (int j = tid; j < n; j += nt) {
+                float2 t = a32[k * n + j];
+                a32[k * n + j] = a32[p * n + j];
+                a32[p * n + j] = t;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            float2 d = a32[k * n + k];
+            float den = d.x * d.x + d.y * d.y;
+            s_inv = make_float2(d.x / den, -d.y / den);
+        }
+        __syncthreads();
+        float2 inv = s_inv;
+        for (int j = tid; j < n; j += nt) a32[k * n + j] = (j == k) ? inv : fmul(a32[k * n + j], inv);
+        for (int i = tid; i < n; i += nt) colk[i] = a32[i * n + k];
+        __syncthreads();
+        for (int e = tid; e < n * n; e += nt) {
+            int i = e / n, j = e - i * n;
+            if (i == k) continue;
+            float2 f = colk[i];
+            if (j == k) {
+                float2 t = fmul(f, inv);
+                a32[e] = make_float2(-t.x, -t.y);
+            } else {
+                float2 t = fmul(f, a32[k * n + j]);
+                a32[e] = make_float2(a32[e].x - t.x, a32[e].y - t.y);
+            }
+        }
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        int p = piv[k];
+        if (p != k) {
+            for (int i = tid; i < n; i += nt) {
+                float2 t = a32[i * n + k];
+                a32[i * n + k] = a32[i * n + p];
+                a32[i * n + p] = t;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < n * n; e += nt) {
+        long long gidx = (long long)(e / n) * ld + (e % n);
+        re[gidx] = a32[e].x;
+        im[gidx] = a32[e].y;
+    }
+}
+
+// C block <- -V, B block <- -V^T (planar float32).
+__global__ void k_negoff32(float *Bre, float *Bim, float *Cre, float *Cim, long long ld, const float *Vre,
+                           const float *Vim, int h) {
+    __shared__ float tr[32][33], ti[32][33];
+    int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    int tx = threadIdx.x, ty = threadIdx.y;
+    for (int i = ty; i < 32; i += 8) {
+        int gi = i0 + i, gj = j0 + tx;
+        if (gi < h && gj < h) {
+            float vr = Vre[(long long)gi * h + gj], vi = Vim[(long long)gi * h + gj];
+            Cre[(long long)gi * ld + gj] = -vr;
+            Cim[(long long)gi * ld + gj] = -vi;
+            tr[i][tx] = vr; ti[i][tx] = vi;
+        }
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        int gj = j0 + i, gi = i0 + tx;  // B[gj][gi] = -V[gi][gj]
+        if (gi < h && gj < h) {
+            Bre[(long long)gj * ld + gi] = -tr[tx][i];
+            Bim[(long long)gj * ld + gi] = -ti[tx][i];
+        }
+    }
+}
+
+// E[c][x] = (R ? R[c][x] : 0) + O[c][x] for c < mcols;  E = R for c >= mcols.
+__global__ void k_combine(double2 *E, const double2 *R, const float *Ore, const float *Oim, int ncol, int mcols,
+                          int nx) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (x >= nx) return;
+    long long i = (long long)c * nx + x;
+    double2 v = R ? R[i] : cmk(0, 0);
+    if (c < mcols) { v.x += (double)Ore[i]; v.y += (double)Oim[i]; }
+    E[i] = v;
+    (void)ncol;
+}
+
+// out = Sigma in, Sigma = U diag(sigma) U^H (a circulant), per column:
+// inverse DFT of sigma times the DFT of the column.
+__global__ void k_circ_apply(const double2 *in, double2 *out, int n, int logn, const double2 *sigma,
+                             const double2 *tw) {
+    extern __shared__ double2 a[];
+    const double2 *src = in + (long long)blockIdx.x * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a[__brev((unsigned)i) >> (32 - logn)] = src[i];
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int lh = 0; lh < logn; ++lh) {
+            int half = 1 << lh, tstride = n >> (lh + 1);
+            for (int t = threadIdx.x; t < n / 2; t += blockDim.x) {
+                int pos = t & (half - 1);
+                int i = ((t >> lh) << (lh + 1)) + pos, j = i + half;
+                double2 w = tw[pos * tstride];
+                if (pass == 1) w.y = -w.y;
+                double2 u = a[i], v = cmul(a[j], w);
+                a[i] = cadd(u, v);
+                a[j] = csub(u, v);
+            }
+            __syncthreads();
+        }
+        if (pass == 0) {
+            // multiply by sigma[m] and bit-reverse for the inverse transform
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                unsigned r = __brev((unsigned)i) >> (32 - logn);
+                if ((int)r > i) {
+                    double2 x = cmul(a[i], sigma[i]), y = cmul(a[r], sigma[r]);
+                    a[i] = y;
+                    a[r] = x;
+                } else if ((int)r == i) {
+                    a[i] = cmul(a[i], sigma[i]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    double2 *dst = out + (long long)blockIdx.x * n;
+    double s = 1.0 / n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = cscale(a[i], s);
+}
+
+// r_j = R_j - K E restricted to the slab, float64.
+__global__ void k_residual(GridDev g, const double *eps, const double2 *E, const double2 *R, const double2 *cb,
+                           const double2 *ct, double2 *r, int ncol) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y, j = blockIdx.z;
+    int n = g.nx;
+    if (x >= n) return;
+    long long L = (long long)ncol * n;
+    const double2 *e = E + j * L + (long long)c * n;
+    double d = 4.0 - g.k * g.k * eps[(long long)j * n + x];
+    double2 v = cscale(e[x], d);
+    v = csub(v, e[(x + 1) % n]);
+    v = csub(v, e[(x + n - 1) % n]);
+    if (j > 0) v = csub(v, e[x - L]);
+    if (j < g.h - 1) v = csub(v, e[x + L]);
+    if (j == 0) v = cadd(v, cb[(long long)c * n + x]);
+    if (j == g.h - 1) v = cadd(v, ct[(long long)c * n + x]);
+    long long idx = j * L + (long long)c * n + x;
+    r[idx] = csub(R[idx], v);
+}
+
+// out[c] = sum_{j,x} |X_j[c][x]|^2 (one block per column, fixed order).
+__global__ void k_colnorm(const double2 *X, int h, int ncol, int nx, double *out) {
+    __shared__ double red[256];
+    int c = blockIdx.x;
+    double acc = 0.0;
+    for (int j = 0; j < h; ++j) {
+        const double2 *p = X + ((long long)j * ncol + c) * nx;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) acc += cabs2(p[x]);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0];
+}
+
+__global__ void k_axpy(double2 *E, const double2 *d, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) E[i] = cadd(E[i], d[i]);
+}
+
+__global__ void k_grad_rowdot32(const double2 *E, const float *Qre, const float *Qim, int j, int nx, int n_in,
+                                int n_out, double k2, double *g) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    int ncol = n_in + n_out;
+    const double2 *phi = E + ((long long)j * ncol + n_in) * nx + x;
+    double acc = 0.0;
+    for (int b = 0; b < n_out; ++b) {
+        double2 p = phi[(long long)b * nx];
+        acc += p.x * (double)Qre[(long long)b * nx + x] - p.y * (double)Qim[(long long)b * nx + x];
+    }
+    g[(long long)j * nx + x] = 2.0 * k2 * acc;
+}
+
+long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+template <typename T>
+int walloc(apf_ctx *c, MixedWork *w, T **p, long long count) {
+    void *q = nullptr;
+    size_t bytes = (size_t)std::max<long long>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(c, APF_ENOMEM, "cudaMalloc(%zu) for the mixed workspace failed", bytes);
+    }
+    w->allocs.push_back(q);
+    c->ws_bytes += (long long)bytes;
+    *p = (T *)q;
+    return APF_OK;
+}
+
+// ---- host-side helpers ----------------------------------------------------
+struct PV {  // planar complex view
+    float *re, *im;
+    long long ld;
+    PV off(long long r, long long c) const { return PV{re + r * ld + c, im + r * ld + c, ld}; }
+};
+
+PackView pack32(apf_ctx *c, __nv_bfloat16 *dst, const PV &src, int R, int K, bool trans, bool layoutB, int nsplit,
+                cudaStream_t s) {
+    long long kp = round_up(2LL * K, 64);
+    long long rows = layoutB ? 2LL * R : R;
+    if (kp != 2LL * K) cudaMemsetAsync(dst, 0, sizeof(__nv_bfloat16) * rows * kp * nsplit, s);
+    dim3 grid((K + 31) / 32, (R + 31) / 32);
+    APF_LAUNCH(c, k_pack32, grid, dim3(32, 8), 0, s, src.re, src.im, src.ld, R, K, trans ? 1 : 0, layoutB ? 1 : 0,
+               nsplit, dst, kp, rows * kp);
+    return PackView{dst, rows, kp, nsplit, rows * kp};
+}
+
+PackView pack64A(apf_ctx *c, __nv_bfloat16 *dst, const double2 *s1, const double2 *s2, long long ld, int R, int K,
+                 int nsplit, cudaStream_t s) {
+    long long kp = round_up(2LL * K, 64);
+    if (kp != 2LL * K) cudaMemsetAsync(dst, 0, sizeof(__nv_bfloat16) * R * kp * nsplit, s);
+    dim3 grid((K + 255) / 256, R);
+    APF_LAUNCH(c, k_pack64_A, grid, 256, 0, s, s1, s2, ld, R, K, nsplit, dst, kp, (long long)R * kp);
+    return PackView{dst, R, kp, nsplit, (long long)R * kp};
+}
+
+PackView pack64BT(apf_ctx *c, __nv_bfloat16 *dst, const double2 *src, long long ld, int R, int K, int nsplit,
+                  cudaStream_t s) {
+    long long kp = round_up(2LL * K, 64);
+    long long rows = 2LL * R;
+    if (kp != 2LL * K) cudaMemsetAsync(dst, 0, sizeof(__nv_bfloat16) * rows * kp * nsplit, s);
+    dim3 grid((K + 31) / 32, (R + 31) / 32);
+    APF_LAUNCH(c, k_pack64_BT, grid, dim3(32, 8), 0, s, src, ld, R, K, nsplit, dst, kp, rows * kp);
+    return PackView{dst, rows, kp, nsplit, rows * kp};
+}
+
+int leaf_size(const MixedWork *w) { return w->leaf; }
+
+// X <- X^-1 in place for complex-symmetric X, the 2x2 block Schur recursion of
+// the float64 path with all four products on the tensor cores.
+int inv32(apf_ctx *c, const PV &X, int n, float *Tre, float *Tim, float *Vre, float *Vim, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    if (n <= leaf_size(w)) {
+        int threads = n >= 64 ? 512 : 256;
+        APF_LAUNCH(c, k_leaf_inv32, 1, threads, n * n * (int)sizeof(float2), s, X.re, X.im, X.ld, n, c->d_flags);
+        return APF_OK;
+    }
+    int h = n / 2;
+    int ns = w->nsplit_elim;
+    PV A = X, B = X.off(0, h), C = X.off(h, 0), D = X.off(h, h);
+    PV T{Tre, Tim, h}, V{Vre, Vim, h};
+    long long hh = (long long)h * h;
+    int rc;
+    if ((rc = inv32(c, A, h, Tre + hh, Tim + hh, Vre + hh, Vim + hh, s))) return rc;
+    // T = C Ai
+    PackView pa = pack32(c, w->PA, C, h, h, false, false, ns, s);
+    PackView pb = pack32(c, w->PB, A, h, h, false, true, ns, s);
+    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, 1.f, 0.f, T.re, T.im, T.ld, nullptr, nullptr, 0, s))) return rc;
+    // D = D - T B   (B-operand columns = rows of C)
+    pa = pack32(c, w->PA, T, h, h, false, false, ns, s);
+    pb = pack32(c, w->PB, C, h, h, false, true, ns, s);
+    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, -1.f, 1.f, D.re, D.im, D.ld, D.re, D.im, D.ld, s))) return rc;
+    if ((rc = inv32(c, D, h, Tre + hh, Tim + hh, Vre + hh, Vim + hh, s))) return rc;
+    // V = Si T
+    pa = pack32(c, w->PA, D, h, h, false, false, ns, s);
+    pb = pack32(c, w->PB, T, h, h, true, true, ns, s);
+    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, 1.f, 0.f, V.re, V.im, V.ld, nullptr, nullptr, 0, s))) return rc;
+    // A = Ai + V^T T
+    pa = pack32(c, w->PA, V, h, h, true, false, ns, s);
+    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, 1.f, 1.f, A.re, A.im, A.ld, A.re, A.im, A.ld, s))) return rc;
+    dim3 grid((h + 31) / 32, (h + 31) / 32);
+    APF_LAUNCH(c, k_negoff32, grid, dim3(32, 8), 0, s, B.re, B.im, C.re, C.im, X.ld, V.re, V.im, h);
+    return APF_OK;
+}
+
+// E ~= Khat^-1 Rin with the stored G_j (block forward sweep + back
+// substitution).  mcols: columns that the forward sweep must carry.
+int approx_solve(apf_ctx *c, const double2 *Rin, double2 *Eout, int mcols, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    int nx = c->nx, ns = w->nsplit_elim;
+    long long L = (long long)ncol * nx;
+    float *Ore = w->O32, *Oim = w->O32 + L;
+    long long gp_rows = 2LL * nx, gp_kp = 2LL * nx;
+    auto gview = [&](int j) {
+        return PackView{w->GP + j * w->gp_stride, gp_rows, gp_kp, ns, gp_rows * gp_kp};
+    };
+    dim3 cgrid((nx + 255) / 256, ncol);
+    cudaMemcpyAsync(Eout, Rin, sizeof(double2) * L, cudaMemcpyDeviceToDevice, s);
+    int rc;
+    for (int j = 1; j < c->h; ++j) {
+        PackView pa = pack64A(c, w->PA, Eout + (j - 1) * L, nullptr, nx, mcols, nx, ns, s);
+        if ((rc = tc_gemm(c, pa, gview(j - 1), ns, mcols, 2 * nx, nx, 1.f, 0.f, Ore, Oim, nx, nullptr, nullptr, 0, s)))
+            return rc;
+        APF_LAUNCH(c, k_combine, cgrid, 256, 0, s, Eout + j * L, Rin + j * L, Ore, Oim, ncol, mcols, nx);
+    }
+    for (int j = c->h - 1; j >= 0; --j) {
+        const double2 *s2 = (j == c->h - 1) ? nullptr : Eout + (j + 1) * L;
+        PackView pa = pack64A(c, w->PA, Eout + j * L, s2, nx, ncol, nx, ns, s);
+        if ((rc = tc_gemm(c, pa, gview(j), ns, ncol, 2 * nx, nx, 1.f, 0.f, Ore, Oim, nx, nullptr, nullptr, 0, s)))
+            return rc;
+        APF_LAUNCH(c, k_combine, cgrid, 256, 0, s, Eout + j * L, (const double2 *)nullptr, Ore, Oim, ncol, ncol, nx);
+    }
+    return APF_OK;
+}
+
+int residual(apf_ctx *c, const double2 *E, double2 *r, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    int nx = c->nx;
+    long long L = (long long)ncol * nx;
+    int logn = 0;
+    while ((1 << logn) < nx) ++logn;
+    int threads = nx / 2 < 256 ? nx / 2 : 256;
+    int smem = nx * (int)sizeof(double2);
+    APF_LAUNCH(c, k_circ_apply, ncol, threads, smem, s, E, w->cb, nx, logn, c->d_modes, c->d_tw);
+    APF_LAUNCH(c, k_circ_apply, ncol, threads, smem, s, E + (c->h - 1) * L, w->ct, nx, logn, c->d_modes + nx,
+               c->d_tw);
+    GridDev g = make_grid(c);
+    dim3 grid((nx + 255) / 256, ncol, c->h);
+    APF_LAUNCH(c, k_residual, grid, 256, 0, s, g, c->d_eps, E, c->d_R, w->cb, w->ct, r, ncol);
+    return APF_OK;
+}
+
+}  // namespace
+
+void mixed_init_attrs() {
+    tc_init_attrs();
+    cudaFuncSetAttribute(k_leaf_inv32, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * (int)sizeof(float2));
+    cudaFuncSetAttribute(k_circ_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * (int)sizeof(double2));
+}
+
+void mixed_free(apf_ctx *c) {
+    if (!c->mw) return;
+    for (void *p : c->mw->allocs) cudaFree(p);
+    delete c->mw;
+    c->mw = nullptr;
+}
+
+int mixed_alloc(apf_ctx *c) {
+    mixed_free(c);
+    MixedWork *w = new MixedWork();
+    c->mw = w;
+    long long n = c->nx, h = c->h;
+    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size();
+    long long ncol = nin + nout;
+    int rc;
+#define WA(p, cnt) if ((rc = walloc(c, w, &(p), (cnt))) != APF_OK) return rc;
+    WA(w->Xre, n * n); WA(w->Xim, n * n);
+    WA(w->Tre, n * n / 2); WA(w->Tim, n * n / 2); WA(w->Vre, n * n / 2); WA(w->Vim, n * n / 2);
+    int ns_max = std::max(w->nsplit_elim, w->nsplit_grad);
+    // A operands: recursion (h x 2h), fields (ncol x 2n), Gamma (n_out x kp)
+    long long kp_g = round_up(2LL * nin, 64);
+    w->pa_elems = std::max({(n / 2) * n * w->nsplit_elim, ncol * 2 * n * w->nsplit_elim, (long long)nout * kp_g * ns_max});
+    // B operands: recursion (2h x 2h), gradient (2n x kp_g)
+    w->pb_elems = std::max(n * n * w->nsplit_elim, 2 * n * kp_g * ns_max);
+    WA(w->PA, w->pa_elems);
+    WA(w->PB, w->pb_elems);
+    w->gp_stride = 2 * n * 2 * n * w->nsplit_elim;
+    WA(w->GP, h * w->gp_stride);
+    WA(w->O32, 2 * std::max<long long>(ncol, nout) * n);
+    WA(w->r, h * ncol * n); WA(w->delta, h * ncol * n);
+    WA(w->cb, ncol * n); WA(w->ct, ncol * n);
+    WA(w->rnorm, 2 * ncol);
+#undef WA
+    return APF_OK;
+}
+
+int mixed_eliminate(apf_ctx *c, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    if (!w) return set_err(c, APF_ESTATE, "mixed workspace missing");
+    GridDev g = make_grid(c);
+    int n = c->nx;
+    dim3 agrid((n + 255) / 256, n);
+    PV X{w->Xre, w->Xim, n};
+    APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, 0, c->d_eps, c->d_circ, (const float *)nullptr,
+               (const float *)nullptr, w->Xre, w->Xim);
+    for (int j = 0; j < c->h; ++j) {
+        int rc = inv32(c, X, n, w->Tre, w->Tim, w->Vre, w->Vim, s);
+        if (rc) return rc;
+        pack32(c, w->GP + j * w->gp_stride, X, n, n, false, true, w->nsplit_elim, s);
+        if (j + 1 < c->h)
+            APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, j + 1, c->d_eps, c->d_circ, w->Xre, w->Xim, w->Xre,
+                       w->Xim);
+    }
+    return APF_OK;
+}
+
+int mixed_solve_fields(apf_ctx *c, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    long long L = (long long)ncol * c->nx, total = L * c->h;
+    // the right-hand side R (rows 0 and h-1 only) was written into d_E by the caller
+    cudaMemcpyAsync(c->d_R, c->d_E, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s);
+    APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, c->d_R, c->h, ncol, c->nx, w->rnorm);
+    int rc = approx_solve(c, c->d_R, c->d_E, nin, s);
+    if (rc) return rc;
+    std::vector<double> nr(ncol), ne(ncol);
+    int iters = 0;
+    double ratio = 0.0;
+    for (;;) {
+        residual(c, c->d_E, w->r, s);
+        APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, c->nx, w->rnorm + ncol);
+        if (iters == 0) cudaMemcpyAsync(nr.data(), w->rnorm, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(ne.data(), w->rnorm + ncol, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return check_cuda(c, e, "refinement");
+        ratio = 0.0;
+        for (int i = 0; i < ncol; ++i) ratio = std::max(ratio, sqrt(ne[i] / std::max(nr[i], 1e-300)));
+        if (!(ratio == ratio)) { ratio = INFINITY; break; }
+        if (ratio <= c->ir_tol || iters >= c->ir_max) break;
+        if ((rc = approx_solve(c, w->r, w->delta, ncol, s))) return rc;
+        APF_LAUNCH(c, k_axpy, (unsigned)((total + 255) / 256), 256, 0, s, c->d_E, w->delta, total);
+        ++iters;
+    }
+    c->stats.refine_iters = iters;
+    c->stats.residual = ratio;
+    return ratio <= c->ir_tol ? APF_OK : APF_ENOCONV;
+}
+
+// Gradient contraction with tensor-core products: Q_j = Gamma F_j, then
+// g_j(x) = 2 k^2 Re sum_b Phi_j[b][x] Q_j[b][x] in float64.
+int mixed_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    int nx = c->nx, ns = w->nsplit_grad;
+    long long L = (long long)ncol * nx;
+    PackView pa = pack64A(c, w->PA, Gamma, nullptr, nin, nout, nin, ns, s);
+    float *Qre = w->O32, *Qim = w->O32 + (long long)nout * nx;
+    for (int j = 0; j < c->h; ++j) {
+        PackView pb = pack64BT(c, w->PB, c->d_E + j * L, nx, nx, nin, ns, s);
+        int rc = tc_gemm(c, pa, pb, ns, nout, 2 * nx, nx, 1.f, 0.f, Qre, Qim, nx, nullptr, nullptr, 0, s);
+        if (rc) return rc;
+        APF_LAUNCH(c, k_grad_rowdot32, (nx + 255) / 256, 256, 0, s, c->d_E, Qre, Qim, j, nx, nin, nout, c->k * c->k,
+                   c->d_grad);
+    }
+    return APF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Test hooks (not part of the public ABI in include/): exercise the packing +
+// tensor-core GEMM and the mixed recursive inversion in isolation.  They
+// allocate their own temporaries.
+// ---------------------------------------------------------------------------
+extern "C" int apf_debug_cgemm(apf_ctx *c, int m, int n, int k, const float *Are, const float *Aim,
+                               const float *Bre, const float *Bim, float *Cre, float *Cim, int nsplit) {
+    if (!c || m < 1 || n < 1 || k < 1 || nsplit < 1 || nsplit > 3) return APF_EINVAL;
+    cudaSetDevice(c->device);
+    long long kp = round_up(2LL * k, 64);
+    __nv_bfloat16 *pa = nullptr, *pb = nullptr;
+    if (cudaMalloc(&pa, sizeof(__nv_bfloat16) * m * kp * nsplit) != cudaSuccess) return APF_ENOMEM;
+    if (cudaMalloc(&pb, sizeof(__nv_bfloat16) * 2LL * n * kp * nsplit) != cudaSuccess) { cudaFree(pa); return APF_ENOMEM; }
+    int *flags = c->d_flags;
+    int *tmpflags = nullptr;
+    if (!flags) { cudaMalloc(&tmpflags, 16); cudaMemset(tmpflags, 0, 16); c->d_flags = tmpflags; }
+    cudaStream_t s = 0;
+    PackView A = pack32(c, pa, PV{(float *)Are, (float *)Aim, k}, m, k, false, false, nsplit, s);
+    PackView B = pack32(c, pb, PV{(float *)Bre, (float *)Bim, n}, n, k, true, true, nsplit, s);
+    int rc = tc_gemm(c, A, B, nsplit, m, 2 * n, n, 1.f, 0.f, Cre, Cim, n, nullptr, nullptr, 0, s);
+    cudaError_t e = cudaDeviceSynchronize();
+    int fl = 0;
+    cudaMemcpy(&fl, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost);
+    if (tmpflags) { cudaFree(tmpflags); c->d_flags = nullptr; }
+    cudaFree(pa);
+    cudaFree(pb);
+    if (rc) return rc;
+    if (e != cudaSuccess) return check_cuda(c, e, "debug cgemm");
+    if (fl & FLAG_TIMEOUT) return set_err(c, APF_ETIMEOUT, "tc_gemm wait gave up");
+    return APF_OK;
+}
+
+// In-place inverse of an n x n complex-symmetric planar float32 matrix using
+// the workspace of a prepared mixed-precision context (n <= its nx).
+extern "C" int apf_debug_inv32(apf_ctx *c, int n, float *re, float *im, int leaf) {
+    if (!c || !c->mw || n < 1 || n > c->nx || (n & (n - 1))) return APF_EINVAL;
+    cudaSetDevice(c->device);
+    int old = c->mw->leaf;
+    if (leaf > 0) c->mw->leaf = leaf;
+    cudaMemset(c->d_flags, 0, 16);
+    int rc = inv32(c, PV{re, im, n}, n, c->mw->Tre, c->mw->Tim, c->mw->Vre, c->mw->Vim, 0);
+    cudaError_t e = cudaDeviceSynchronize();
+    c->mw->leaf = old;
+    if (rc) return rc;
+    if (e != cudaSuccess) return check_cuda(c, e, "debug inv32");
+    int fl = 0;
+    cudaMemcpy(&fl, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost);
+    if (fl & FLAG_TIMEOUT) return set_err(c, APF_ETIMEOUT, "tc_gemm wait gave up");
+    if (fl & FLAG_SINGULAR) return set_err(c, APF_ESINGULAR, "singular leaf");
+    return APF_OK;
+}

@@ -113,7 +113,8 @@ int launch_objective(apf_ctx *c, int objective, const double *params, int n_para
     return APF_OK;
 }
 
-void launch_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s) {
+int launch_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s) {
+    if (c->precision != APF_FP64) return mixed_gradient(c, Gamma, s);
     int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
     long long nx = c->nx;
     // Q_j = Gamma (n_out x n_in) * F_j (n_in x nx), batched over the slab rows
@@ -121,4 +122,5 @@ void launch_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s) {
           c->d_Q, nx, (long long)nout * nx, c->h, s);
     dim3 grid((c->nx + 255) / 256, c->h);
     APF_LAUNCH(c, k_grad_rowdot, grid, 256, 0, s, c->d_E, c->d_Q, c->h, c->nx, nin, nout, c->k * c->k, c->d_grad);
+    return APF_OK;
 }

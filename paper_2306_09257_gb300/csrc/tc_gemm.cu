@@ -1,0 +1,330 @@
+// Tensor-core GEMM for sm_103a: tcgen05.mma (kind::f16, bf16 operands, fp32
+// accumulation in tensor memory), operands staged by TMA with 128-byte
+// swizzle, warp-specialized (1 TMA producer warp, 1 MMA-issuing warp, 4
+// epilogue warps).
+//
+// The GEMM is real: D[m][n] = sum_k A[m][k] B[n][k] with A and B "K-major"
+// (rows contiguous in k).  Complex products and extra precision are both
+// expressed through the operand layout, so one real kernel serves all of the
+// slab elimination:
+//   * complex: A-row = [Re a, Im a], B-rows = [Re b, -Im b] (real part of the
+//     output) and [Im b, Re b] (imaginary part), so a complex m x k x n product
+//     is one real m x 2k x 2n product;
+//   * precision: each operand is split into 2 or 3 bf16 planes
+//     (x = x0 + x1 [+ x2]); the kernel walks "segments", one per retained
+//     plane product (x0 y0, x0 y1, x1 y0 [, x0 y2, x1 y1, x2 y0]), all
+//     accumulated in the same fp32 tensor-memory tile.
+// Operand planes live in 3-D tensor maps (k, row, plane), so rows past the
+// operand's end are zero-filled by TMA and no padding is needed in m or n.
+#include "apf_internal.h"
+#include "tc_gemm.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;  // bf16 elements per 128-byte swizzle row
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^31 clock cycles (about a second) or when
+// another role of this block has already given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          bool ignore_abort = false) {
+    long long t0 = clock64();
+    uint32_t spins = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if ((++spins & 1023u) == 0) {
+            if (!ignore_abort && *abort_flag) return false;
+            if (clock64() - t0 > (1ll << 31)) return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *smem_dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];" ::"r"(smem_u32(smem_dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// atoms of 1024 bytes (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN, int STAGES>
+struct Layout {
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int BAR = STAGES * STAGE;
+    static constexpr int TOTAL = BAR + (2 * STAGES + 1) * 8 + 16 + 1024;
+};
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+    using L = Layout<BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + L::BAR);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accb = empty + STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(accb + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int total = p.nseg * p.kblocks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accb, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    int issued = 0;
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int it = 0; it < total; ++it) {
+                int s = it % STAGES, r = it / STAGES;
+                if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) { ok = false; break; }
+                int seg = it / p.kblocks, kb = it - seg * p.kblocks;
+                int pa = (p.seg_pairs >> (4 * seg + 2)) & 3, pb = (p.seg_pairs >> (4 * seg)) & 3;
+                uint8_t *sa = smem + s * L::STAGE;
+                uint8_t *sb = sa + L::A_BYTES;
+                mbar_expect_tx(&full[s], L::A_BYTES + L::B_BYTES);
+                tma_load_3d(sa, &tmA, &full[s], kb * BK, m0, pa);
+                tma_load_3d(sb, &tmB, &full[s], kb * BK, n0, pb);
+                issued = it + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                   ((uint32_t)(BM >> 4) << 24);
+            for (int it = 0; it < total; ++it) {
+                int s = it % STAGES, r = it / STAGES;
+                if (!mbar_wait(&full[s], r & 1, abort_flag)) { ok = false; break; }
+                fence_after();
+                uint32_t sa = smem_u32(smem + s * L::STAGE);
+                uint32_t sb = sa + L::A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    mma_bf16(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
+                             (it > 0 || kk > 0) ? 1u : 0u);
+                }
+                mma_commit(&empty[s]);
+            }
+            mma_commit(accb);
+            // on failure, let the MMAs already issued drain before TMEM is freed
+            if (!ok) mbar_wait(accb, 0, abort_flag, true);
+        }
+    } else {
+        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        if (!mbar_wait(accb, 0, abort_flag)) {
+            ok = false;
+        } else {
+            fence_after();
+            const int row = m0 + 32 * q + lane;
+            const bool use_beta = (p.beta != 0.0f);
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, r);
+                if (row < p.M) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        int col = n0 + c + i;
+                        if (col >= p.N) break;
+                        float *op;
+                        const float *ip;
+                        int cc;
+                        if (col < p.n_cplx) { op = p.out_re; ip = p.in_re; cc = col; }
+                        else { op = p.out_im; ip = p.in_im; cc = col - p.n_cplx; }
+                        float v = p.alpha * __uint_as_float(r[i]);
+                        if (use_beta) v += p.beta * ip[(long long)row * p.ldi + cc];
+                        op[(long long)row * p.ldo + cc] = v;
+                    }
+                }
+            }
+        }
+    }
+    if (!ok) {
+        *abort_flag = 1;
+        if (p.flags) atomicOr(p.flags, FLAG_TIMEOUT);
+    }
+    __syncwarp();
+    // after a failure anywhere, wait (bounded) for the producer's copies in flight
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        for (int it = issued > STAGES ? issued - STAGES : 0; it < issued; ++it)
+            mbar_wait(&full[it % STAGES], (it / STAGES) & 1, abort_flag, true);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool ensure_encode() {
+    if (g_encode) return true;
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return false;
+    }
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return true;
+}
+
+bool make_map(CUtensorMap *m, const PackView &v, int box_rows) {
+    cuuint64_t dims[3] = {(cuuint64_t)v.kp, (cuuint64_t)v.rows, (cuuint64_t)v.planes};
+    cuuint64_t strides[2] = {(cuuint64_t)v.kp * 2, (cuuint64_t)v.plane_pitch * 2};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)v.base, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES>
+void set_attr() {
+    cudaFuncSetAttribute(k_tc_gemm<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Layout<BN, STAGES>::TOTAL);
+}
+
+}  // namespace
+
+// Segment lists: (a plane, b plane) per retained product of split planes.
+uint32_t tc_seg_pairs(int nsplit, int *nseg) {
+    if (nsplit == 1) { *nseg = 1; return 0u; }
+    if (nsplit == 2) {
+        *nseg = 3;  // x0y0, x0y1, x1y0
+        return (0u << 0) | ((0u << 2 | 1u) << 4) | ((1u << 2 | 0u) << 8);
+    }
+    *nseg = 6;  // + x0y2, x1y1, x2y0
+    return (0u) | ((0u << 2 | 1u) << 4) | ((1u << 2 | 0u) << 8) | ((0u << 2 | 2u) << 12) | ((1u << 2 | 1u) << 16) |
+           ((2u << 2 | 0u) << 20);
+}
+
+void tc_init_attrs() {
+    set_attr<256, 4>();
+    set_attr<128, 6>();
+}
+
+int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M, int N, int n_cplx, float alpha,
+            float beta, float *out_re, float *out_im, long long ldo, const float *in_re, const float *in_im,
+            long long ldi, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return APF_OK;
+    if (!ensure_encode()) return set_err(c, APF_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    if (A.kp != B.kp || A.kp % BK != 0) return set_err(c, APF_EINVAL, "tc_gemm: K mismatch (%lld vs %lld)", A.kp, B.kp);
+    TcParams p{};
+    p.M = M; p.N = N; p.n_cplx = n_cplx;
+    p.kblocks = (int)(A.kp / BK);
+    p.seg_pairs = tc_seg_pairs(nsplit, &p.nseg);
+    p.alpha = alpha; p.beta = beta;
+    p.out_re = out_re; p.out_im = out_im; p.ldo = ldo;
+    p.in_re = in_re ? in_re : out_re; p.in_im = in_im ? in_im : out_im; p.ldi = in_re ? ldi : ldo;
+    p.flags = c->d_flags;
+    CUtensorMap ma, mb;
+    // Wide tiles when they still fill the GPU; otherwise 128-wide tiles.
+    long long tiles256 = (long long)((N + 255) / 256) * ((M + BM - 1) / BM);
+    bool wide = (N > 128) && tiles256 >= 120;
+    int bn = wide ? 256 : 128;
+    if (!make_map(&ma, A, BM) || !make_map(&mb, B, bn))
+        return set_err(c, APF_ECUDA, "tensor map encode failed (M=%d N=%d kp=%lld)", M, N, A.kp);
+    dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM);
+    constexpr int smem_wide = Layout<256, 4>::TOTAL, smem_narrow = Layout<128, 6>::TOTAL;
+    if (wide) APF_LAUNCH(c, (k_tc_gemm<256, 4>), grid, 192, smem_wide, s, ma, mb, p);
+    else APF_LAUNCH(c, (k_tc_gemm<128, 6>), grid, 192, smem_narrow, s, ma, mb, p);
+    return APF_OK;
+}
