@@ -28,7 +28,7 @@ def planar(torch, z):
 
 # (m, n, k): aligned, ragged m/n/k, and a size that fills the GPU with wide tiles.
 SHAPES = [(128, 256, 64), (200, 130, 96), (37, 300, 40), (1024, 2048, 512)]
-TOL = {1: 1.5e-2, 2: 1e-4, 3: 3e-6}
+TOL = {1: 1.5e-2, 2: 1e-4, 3: 3e-5}  # 3 planes: limited by the tensor-core fp32 accumulation
 
 
 @pytest.mark.parametrize("nsplit", [1, 2, 3])
