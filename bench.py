@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Throughput of S + df/deps evaluations on GB300 (one JSON line on rank 0).
+
+A step is one full pass of the hot path for one permittivity map: per-mode
+boundary elimination, slab block-Schur elimination, forward + adjoint field
+sweeps with float64 refinement, S readout, beam-splitter objective (Eq. 5,
+relative orders -2..2, target 0.18) and the adjoint gradient for every slab
+pixel.  Inputs are synthetic filtered-threshold metasurfaces (seeded).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Multi-GPU: one evaluation does not shard, so N ranks run N independent
+replicas (different seeds), no collective on the data path ("weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2306_09257_gb300 import workloads as W  # noqa: E402
+
+METRIC = "S+grad evals/s, mixed vs FP64 on 1 GB300 at stated err; % of tensor peak"
+ORDERS = [-2, -1, 0, 1, 2]
+TARGET = 0.18
+WL = {"mid": W.MID, "large": W.LARGE, "xlarge": W.XLARGE, "tiny": W.TINY}
+
+
+def args_parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="large", choices=sorted(WL))
+    p.add_argument("--fp64-steps", type=int, default=1, help="timed float64 steps for the comparison (0 = skip)")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--solves", type=int, default=4, help="oracle solves per CPU sample")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.gpu), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cpu_oracle_sample(w, eps, nsolve):
+    """Bounded sample of the oracle on the host: assemble + factor A once,
+    time `nsolve` forward and `nsolve` adjoint solves, and extrapolate to one
+    full evaluation (M_in forward + M_in adjoint solves, Eq. S1)."""
+    import scipy.sparse.linalg as spla
+
+    import oracle as O
+    pb = O.problem_from_workload(w, eps)
+    t0 = time.perf_counter()
+    A = O.assemble_A(pb)
+    lu = spla.splu(A)
+    t_fac = time.perf_counter() - t0
+    m_in, m_out = pb.inputs(), pb.outputs()
+    B = O.source_matrix(pb, m_in[:nsolve], pb.j_src, pb.eps_sub)
+    C = O.projection_matrix(pb, m_out, pb.j_out, pb.eps_clad)
+    t1 = time.perf_counter()
+    for a in range(B.shape[1]):
+        x = lu.solve(B[:, a])
+        lu.solve(C[a % C.shape[0]].copy(), trans="T")
+    t_solve = (time.perf_counter() - t1) / (2 * B.shape[1])
+    t_eval = t_fac + 2 * len(m_in) * t_solve
+    return t_eval, t_fac, t_solve, len(m_in)
+
+
+def run_reference(a, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    eps = w.eps_slab(0)
+    # one factorization (measured, counted in every evaluation) + per step a
+    # bounded slice of the 2*M_in solves
+    import scipy.sparse.linalg as spla
+
+    import oracle as O
+    pb = O.problem_from_workload(w, eps)
+    t0 = time.perf_counter()
+    A = O.assemble_A(pb)
+    lu = spla.splu(A)
+    t_fac = time.perf_counter() - t0
+    m_in, m_out = pb.inputs(), pb.outputs()
+    B = O.source_matrix(pb, m_in, pb.j_src, pb.eps_sub)
+    C = O.projection_matrix(pb, m_out, pb.j_out, pb.eps_clad)
+    ts = []
+    for step in range(a.warmup + a.steps):
+        t1 = time.perf_counter()
+        for i in range(a.solves):
+            col = (step * a.solves + i) % B.shape[1]
+            lu.solve(B[:, col])
+            lu.solve(C[col % C.shape[0]].copy(), trans="T")
+        dt = (time.perf_counter() - t1) / (2 * a.solves)
+        if step >= a.warmup:
+            ts.append(dt)
+    t_eval = t_fac + 2 * len(m_in) * statistics.mean(ts)
+    v = 1.0 / t_eval
+    sample = (f"assemble+SuperLU factor once ({t_fac:.1f} s), then per step {a.solves} forward + {a.solves} "
+              f"adjoint solves; evaluation time = factor + 2*{len(m_in)} solves")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * t_eval, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "h": w.h, "channels": len(m_in),
+                       "objective": "beam splitter, orders -2..2, t=0.18"},
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args_parse()
+    w = WL[a.workload]
+    ws, rank, local = dist_env()
+    if a.impl == "reference":
+        run_reference(a, w)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_2306_09257_gb300 import apf
+
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nseeds = 4
+    eps_host = [w.eps_slab(1000 * rank + i) for i in range(nseeds)]
+    eps_dev = [torch.tensor(e, device=dev) for e in eps_host]
+    s = apf.solver_for_workload(w, eps_host[0], precision="mixed", device=local)
+    m_in, m_out = s.channels()
+    S_d = torch.empty((len(m_out), len(m_in)), dtype=torch.complex128, device=dev)
+    g_d = torch.empty((w.h, w.nx), dtype=torch.float64, device=dev)
+
+    def step(i):
+        s.set_eps(eps_dev[i % nseeds], w.eps_sub, w.eps_clad, j0=w.j0)
+        return s.solve_S_grad("splitter", ORDERS, TARGET, out_S=S_d, out_grad=g_d)
+
+    for i in range(a.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    s.set_profiling(True)
+    clk = Clocks(local)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    launches, iters = 0, []
+    for i in range(a.steps):
+        step(i)
+        st = s.stats()
+        launches += st["kernel_launches"]
+        iters.append(st["refine_iters"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    prof = s.profile()
+    s.set_profiling(False)
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * a.steps / (ms / 1000.0)
+    st_last = s.stats()
+
+    # end to end through the public API with host buffers (H2D eps, D2H S/grad/f)
+    e2e_t = []
+    for i in range(a.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_eps(eps_host[i % nseeds], w.eps_sub, w.eps_clad, j0=w.j0)
+        S_h, f_h, g_h = s.solve_S_grad("splitter", ORDERS, TARGET)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = ws * 1.0 / statistics.mean(e2e_t) if e2e_t else None
+    h2d = w.h * w.nx * 8
+    d2h = len(m_in) * len(m_out) * 16 + w.h * w.nx * 8 + 8
+
+    # float64 GPU path on the same workload and the mixed-vs-float64 error
+    fp64 = None
+    if a.fp64_steps > 0:
+        s64 = apf.solver_for_workload(w, eps_host[0], precision="fp64", device=local)
+        s64.solve_S_grad("splitter", ORDERS, TARGET)  # warm-up
+        t0 = time.perf_counter()
+        for _ in range(a.fp64_steps):
+            S64, f64v, g64 = s64.solve_S_grad("splitter", ORDERS, TARGET)
+        t64 = (time.perf_counter() - t0) / a.fp64_steps
+        s.set_eps(eps_host[0], w.eps_sub, w.eps_clad, j0=w.j0)
+        Sm, fm, gm = s.solve_S_grad("splitter", ORDERS, TARGET)
+        fp64 = {"value": 1.0 / t64, "unit": "evals/s", "steps": a.fp64_steps,
+                "err_S_mixed_vs_fp64": rel(Sm, S64), "err_grad_mixed_vs_fp64": rel(gm, g64),
+                "speedup_mixed_over_fp64": value / ws * t64}
+        s64.close()
+
+    pk, src = peaks()
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    hw_tf = prof["gemm_hw_flops"] / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else 0.0
+    alg_tf = prof["gemm_alg_flops"] / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else 0.0
+    gemm_share = prof["gemm_ms"] / ms if ms > 0 else 0.0
+    roofline = {"bound": "tensor", "achieved": hw_tf, "peak": peak, "unit": "TFLOP/s", "frac": hw_tf / peak,
+                "traffic": None, "kernel": "k_tc_gemm (tcgen05 bf16, fp32 accumulate)",
+                "achieved_algorithmic_complex_tflops": alg_tf,
+                "note": (f"achieved = bf16 tensor flops (8 m n k per complex product x plane products) / "
+                         f"summed CUDA-event launch time over the timed region; peak = bf16_tflops_sustained "
+                         f"({src}); GEMM time share of step {gemm_share:.2f}")}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        t_eval, t_fac, t_solve, nin = cpu_oracle_sample(w, eps_host[0], a.solves)
+        cpu = {"value": 1.0 / t_eval, "unit": "evals/s", "cores": 1, "kind": "oracle",
+               "sample": (f"SuperLU factor ({t_fac:.1f} s, serial) + {a.solves} forward and {a.solves} adjoint "
+                          f"solves ({t_solve:.3f} s each), extrapolated to 2*{nin} solves per evaluation")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
+                "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "npml": w.npml, "lambda_px": w.lambda_px,
+                           "h": w.h, "channels": [len(m_in), len(m_out)], "eps": "filtered-threshold, seeded",
+                           "objective": "beam splitter Eq. 5, orders -2..2, t=0.18",
+                           "l2": f"working set {st_last['workspace_bytes'] / 1e9:.1f} GB > 129 MB L2, no flush",
+                           "refine_iters": iters, "residual": st_last["residual"],
+                           "parallelism": f"replicas x{ws}"},
+                "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu,
+                "fp64": fp64,
+                "stages_ms": {k: st_last[k] for k in ("ms_boundary", "ms_eliminate", "ms_fields", "ms_readout",
+                                                       "ms_gradient")},
+                "gemm": {"launches": prof["gemm_launches"], "ms": prof["gemm_ms"]}}
+        print(json.dumps(line), flush=True)
+    s.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -138,6 +138,23 @@ int apf_set_refinement(apf_ctx *ctx, double tol, int max_iters);
 
 int apf_get_stats(const apf_ctx *ctx, apf_stats *stats);
 
+/* Measurement support (no counterpart in the paper).  When enabled, every
+   tensor-core GEMM launch of later solves is bracketed by CUDA events on the
+   solve's stream; apf_get_profile returns the totals accumulated since the
+   last apf_set_profiling call.  Flops are counted as real multiply-adds x 2:
+   alg_flops for the complex products the method needs (8 per complex
+   multiply-add), hw_flops for what the tensor pipe executes (alg_flops x the
+   number of bf16 plane products). */
+typedef struct {
+    long long gemm_launches;
+    double gemm_ms;
+    double gemm_alg_flops;
+    double gemm_hw_flops;
+} apf_profile;
+
+int apf_set_profiling(apf_ctx *ctx, int enable);
+int apf_get_profile(const apf_ctx *ctx, apf_profile *prof);
+
 /* Message of the most recent failure on this context (or of apf_create when
    ctx is NULL).  Never NULL. */
 const char *apf_last_error(const apf_ctx *ctx);

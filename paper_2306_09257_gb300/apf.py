@@ -27,7 +27,8 @@ OBJECTIVES = {"power": APF_OBJ_POWER, "splitter": APF_OBJ_SPLITTER}
 # Every symbol that include/apf.h declares.
 EXPORTS = ("apf_create", "apf_destroy", "apf_set_grid", "apf_set_eps", "apf_set_channels",
            "apf_get_channels", "apf_solve_S", "apf_solve_S_grad", "apf_grad_from_gamma",
-           "apf_set_refinement", "apf_get_stats", "apf_last_error", "apf_version")
+           "apf_set_refinement", "apf_get_stats", "apf_set_profiling", "apf_get_profile",
+           "apf_last_error", "apf_version")
 
 
 class APFError(RuntimeError):
@@ -42,6 +43,14 @@ class Stats(ctypes.Structure):
                 ("ms_eliminate", ctypes.c_double), ("ms_fields", ctypes.c_double),
                 ("ms_readout", ctypes.c_double), ("ms_gradient", ctypes.c_double),
                 ("kernel_launches", ctypes.c_longlong), ("workspace_bytes", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("gemm_launches", ctypes.c_longlong), ("gemm_ms", ctypes.c_double),
+                ("gemm_alg_flops", ctypes.c_double), ("gemm_hw_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -75,6 +84,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.apf_grad_from_gamma.argtypes = [vp, dp, dp, vp]
     L.apf_set_refinement.argtypes = [vp, d, i]
     L.apf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.apf_set_profiling.argtypes = [vp, i]
+    L.apf_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
     L.apf_last_error.argtypes = [vp]
     L.apf_last_error.restype = ctypes.c_char_p
     L.apf_version.argtypes = []
@@ -202,6 +213,14 @@ class Solver:
         st = _stream_of(Gamma, g)
         self._check(self._L.apf_grad_from_gamma(self._h, _ptr(Gamma, np.complex128), _ptr(g, np.float64), st))
         return g
+
+    def set_profiling(self, enable: bool = True):
+        self._check(self._L.apf_set_profiling(self._h, 1 if enable else 0))
+
+    def profile(self) -> dict:
+        p = Profile()
+        self._check(self._L.apf_get_profile(self._h, ctypes.byref(p)))
+        return p.as_dict()
 
     def stats(self) -> dict:
         s = Stats()

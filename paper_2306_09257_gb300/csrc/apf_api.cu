@@ -284,6 +284,30 @@ int apf_set_refinement(apf_ctx *c, double tol, int max_iters) {
     return APF_OK;
 }
 
+int apf_set_profiling(apf_ctx *c, int enable) {
+    if (!c) return APF_EINVAL;
+    cudaSetDevice(c->device);
+    c->prof = apf_profile{};
+    c->prof_used = 0;
+    c->prof_on = enable != 0;
+    if (c->prof_on && c->prof_ev.empty()) {
+        const int pairs = 16384;
+        c->prof_ev.resize(2 * pairs);
+        for (auto &e : c->prof_ev) {
+            if (cudaEventCreate(&e) != cudaSuccess) return check_cuda(c, cudaGetLastError(), "profiling events");
+        }
+        c->prof_alg.assign(pairs, 0.0);
+        c->prof_hw.assign(pairs, 0.0);
+    }
+    return APF_OK;
+}
+
+int apf_get_profile(const apf_ctx *c, apf_profile *p) {
+    if (!c || !p) return APF_EINVAL;
+    *p = c->prof;
+    return APF_OK;
+}
+
 int apf_get_stats(const apf_ctx *c, apf_stats *st) {
     if (!c || !st) return APF_EINVAL;
     *st = c->stats;
@@ -352,9 +376,25 @@ static int run_solve(apf_ctx *c, cudaStream_t s) {
     return rc;
 }
 
+// Fold the GEMM events of the finished solve into the profile totals.
+void prof_collect(apf_ctx *c) {
+    for (int i = 0; i < c->prof_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) == cudaSuccess) {
+            c->prof.gemm_launches++;
+            c->prof.gemm_ms += ms;
+            c->prof.gemm_alg_flops += c->prof_alg[i];
+            c->prof.gemm_hw_flops += c->prof_hw[i];
+        }
+    }
+    cudaGetLastError();
+    c->prof_used = 0;
+}
+
 static int finish(apf_ctx *c, cudaStream_t s, int rc_solve) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return check_cuda(c, e, "solve");
+    if (c->prof_on) prof_collect(c);
     e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(c, e, "kernel launch");
     int flags = 0;
@@ -437,6 +477,7 @@ int apf_grad_from_gamma(apf_ctx *c, const double *Gamma, double *grad_eps, void 
     cudaMemcpyAsync(grad_eps, c->d_grad, sizeof(double) * c->h * c->nx, cudaMemcpyDefault, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return check_cuda(c, e, "grad_from_gamma");
+    if (c->prof_on) prof_collect(c);
     float ms = 0;
     cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
     c->stats.ms_gradient = ms;

@@ -97,6 +97,12 @@ struct apf_ctx {
     int *d_flags = nullptr;
     int *d_pairs = nullptr;      // objective (b, a) pairs
     MixedWork *mw = nullptr;
+    // GEMM launch profiling
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;      // pairs
+    std::vector<double> prof_alg, prof_hw; // per recorded pair
+    int prof_used = 0;
+    apf_profile prof{};
     // stats
     apf_stats stats{};
     long long launches = 0;
@@ -147,6 +153,7 @@ int mixed_eliminate(apf_ctx *c, cudaStream_t s);
 int mixed_solve_fields(apf_ctx *c, cudaStream_t s);
 
 int set_err(apf_ctx *c, int code, const char *fmt, ...);
+void prof_collect(apf_ctx *c);
 void slab64_init_attrs();
 void mixed_init_attrs();
 int check_cuda(apf_ctx *c, cudaError_t e, const char *what);

@@ -1,0 +1,144 @@
+// Diagonal-block inversion shared by the float64 and the mixed path:
+// Gauss-Jordan elimination with partial (row) pivoting of one NB x NB block
+// in shared memory.  Thread t owns row t/4 and the columns sub + 4q
+// (sub = t%4), so the 4 threads of a row sit in adjacent lanes and the
+// pivot-row reads are conflict-free; rows are padded by 4 elements.
+// Row interchanges of the sweep become column interchanges of the inverse,
+// undone in reverse order at the end.
+#pragma once
+#include "apf_internal.h"
+
+template <typename R>
+struct Cplx;
+template <>
+struct Cplx<double> {
+    using T = double2;
+    __device__ static T mk(double a, double b) { return make_double2(a, b); }
+};
+template <>
+struct Cplx<float> {
+    using T = float2;
+    __device__ static T mk(float a, float b) { return make_float2(a, b); }
+};
+
+// Planar (re, im) or interleaved global layout.
+template <typename R, bool PLANAR>
+struct LeafIO {
+    R *re, *im;
+    typename Cplx<R>::T *z;
+    long long ld;
+    __device__ typename Cplx<R>::T load(int r, int c) const {
+        long long g = (long long)r * ld + c;
+        if (PLANAR) return Cplx<R>::mk(re[g], im[g]);
+        return z[g];
+    }
+    __device__ void store(int r, int c, typename Cplx<R>::T v) const {
+        long long g = (long long)r * ld + c;
+        if (PLANAR) { re[g] = v.x; im[g] = v.y; }
+        else z[g] = v;
+    }
+};
+
+template <typename R, int NB, bool PLANAR>
+__device__ void leaf_gj(LeafIO<R, PLANAR> io, int *flags) {
+    using T = typename Cplx<R>::T;
+    constexpr int P = NB + 4;
+    constexpr int NT = NB * 4;
+    constexpr int Q = NB / 4;
+    extern __shared__ __align__(16) unsigned char leaf_smem[];
+    T *a = reinterpret_cast<T *>(leaf_smem);
+    __shared__ T rowk[NB], colk[NB];
+    __shared__ R mag[NB];
+    __shared__ int piv[NB];
+    __shared__ int s_p;
+    const int t = threadIdx.x, i = t >> 2, sub = t & 3;
+    for (int e = t; e < NB * NB; e += NT) {
+        int r = e / NB, c = e % NB;  // NB is a compile-time power of two
+        a[r * P + c] = io.load(r, c);
+    }
+    __syncthreads();
+    if (t < NB) {
+        T v = a[t * P];
+        mag[t] = v.x * v.x + v.y * v.y;
+    }
+    __syncthreads();
+    for (int k = 0; k < NB; ++k) {
+        if (t < 32) {
+            R best = (R)-1;
+            int bi = k;
+            for (int r = k + t; r < NB; r += 32) {
+                R m = mag[r];
+                if (m > best) { best = m; bi = r; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                R ob = __shfl_down_sync(0xffffffffu, best, off);
+                int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (t == 0) {
+                s_p = bi;
+                piv[k] = bi;
+                if (!(best > (R)0) || !isfinite((double)best)) atomicOr(flags, FLAG_SINGULAR);
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k && t < NB) {
+            T x = a[k * P + t];
+            a[k * P + t] = a[p * P + t];
+            a[p * P + t] = x;
+        }
+        __syncthreads();
+        if (t < NB) {
+            T d = a[k * P + k];
+            R den = d.x * d.x + d.y * d.y;
+            T inv = Cplx<R>::mk(d.x / den, -d.y / den);
+            T v = a[k * P + t];
+            rowk[t] = (t == k) ? inv : Cplx<R>::mk(v.x * inv.x - v.y * inv.y, v.x * inv.y + v.y * inv.x);
+            colk[t] = a[t * P + k];
+        }
+        __syncthreads();
+        const T f = colk[i];
+        T *row = a + i * P;
+        if (i == k) {
+#pragma unroll 8
+            for (int q = 0; q < Q; ++q) row[sub + 4 * q] = rowk[sub + 4 * q];
+        } else {
+            R m1 = (R)-1;
+#pragma unroll 8
+            for (int q = 0; q < Q; ++q) {
+                const int j = sub + 4 * q;
+                T x = (j == k) ? Cplx<R>::mk(0, 0) : row[j];
+                T rk = rowk[j];
+                x.x -= f.x * rk.x - f.y * rk.y;
+                x.y -= f.x * rk.y + f.y * rk.x;
+                row[j] = x;
+                if (j == k + 1) m1 = x.x * x.x + x.y * x.y;
+            }
+            if (((k + 1) & 3) == sub && k + 1 < NB) mag[i] = m1;
+        }
+        if (i == k && ((k + 1) & 3) == sub && k + 1 < NB) {
+            T x = rowk[k + 1];
+            mag[i] = x.x * x.x + x.y * x.y;
+        }
+        __syncthreads();
+    }
+    for (int k = NB - 1; k >= 0; --k) {
+        int p = piv[k];
+        if (p != k && t < NB) {
+            T x = a[t * P + k];
+            a[t * P + k] = a[t * P + p];
+            a[t * P + p] = x;
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < NB * NB; e += NT) {
+        int r = e / NB, c = e % NB;
+        io.store(r, c, a[r * P + c]);
+    }
+}
+
+template <int NB>
+constexpr int leaf_smem_bytes(int elem_bytes) {
+    return NB * (NB + 4) * elem_bytes;
+}

@@ -11,6 +11,7 @@
 // where Khat^-1 is the block-LU solve with the stored low-precision G_j.
 #include "apf_internal.h"
 #include "tc_gemm.h"
+#include "leaf.cuh"
 
 #include <algorithm>
 #include <vector>
@@ -250,6 +251,12 @@ __global__ void __launch_bounds__(512) k_leaf_inv32(float *re, float *im, long l
     }
 }
 
+template <int NB>
+__global__ void __launch_bounds__(NB * 4) k_leaf32(float *re, float *im, long long ld, int *flags) {
+    LeafIO<float, true> io{re, im, nullptr, ld};
+    leaf_gj<float, NB, true>(io, flags);
+}
+
 // C block <- -V, B block <- -V^T (planar float32).
 __global__ void k_negoff32(float *Bre, float *Bim, float *Cre, float *Cim, long long ld, const float *Vre,
                            const float *Vim, int h) {
@@ -449,8 +456,16 @@ int leaf_size(const MixedWork *w) { return w->leaf; }
 int inv32(apf_ctx *c, const PV &X, int n, float *Tre, float *Tim, float *Vre, float *Vim, cudaStream_t s) {
     MixedWork *w = c->mw;
     if (n <= leaf_size(w)) {
-        int threads = n >= 64 ? 512 : 256;
-        APF_LAUNCH(c, k_leaf_inv32, 1, threads, n * n * (int)sizeof(float2), s, X.re, X.im, X.ld, n, c->d_flags);
+        if (n == 128)
+            APF_LAUNCH(c, k_leaf32<128>, 1, 512, leaf_smem_bytes<128>(8), s, X.re, X.im, X.ld, c->d_flags);
+        else if (n == 64)
+            APF_LAUNCH(c, k_leaf32<64>, 1, 256, leaf_smem_bytes<64>(8), s, X.re, X.im, X.ld, c->d_flags);
+        else if (n == 32)
+            APF_LAUNCH(c, k_leaf32<32>, 1, 128, leaf_smem_bytes<32>(8), s, X.re, X.im, X.ld, c->d_flags);
+        else if (n == 16)
+            APF_LAUNCH(c, k_leaf32<16>, 1, 64, leaf_smem_bytes<16>(8), s, X.re, X.im, X.ld, c->d_flags);
+        else
+            APF_LAUNCH(c, k_leaf_inv32, 1, 256, n * n * (int)sizeof(float2), s, X.re, X.im, X.ld, n, c->d_flags);
         return APF_OK;
     }
     int h = n / 2;
@@ -535,6 +550,8 @@ int residual(apf_ctx *c, const double2 *E, double2 *r, cudaStream_t s) {
 void mixed_init_attrs() {
     tc_init_attrs();
     cudaFuncSetAttribute(k_leaf_inv32, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * (int)sizeof(float2));
+    cudaFuncSetAttribute(k_leaf32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_smem_bytes<128>(8));
+    cudaFuncSetAttribute(k_leaf32<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_smem_bytes<64>(8));
     cudaFuncSetAttribute(k_circ_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * (int)sizeof(double2));
 }
 

@@ -12,6 +12,7 @@
 // the augmented K, obtained here block row by block row).  Every X_j is
 // complex symmetric (reciprocity, A = A^T), which the inversion exploits.
 #include "apf_internal.h"
+#include "leaf.cuh"
 
 namespace {
 
@@ -180,6 +181,12 @@ __global__ void __launch_bounds__(256) k_leaf_inv64(double2 *X, int n, long long
     for (int e = tid; e < n * n; e += nt) X[(long long)(e / n) * ld + (e % n)] = a[e];
 }
 
+template <int NB>
+__global__ void __launch_bounds__(NB * 4) k_leaf64(double2 *X, long long ld, int *flags) {
+    LeafIO<double, false> io{nullptr, nullptr, X, ld};
+    leaf_gj<double, NB, false>(io, flags);
+}
+
 // C block <- -V, B block <- -V^T  (the off-diagonal blocks of the inverse).
 __global__ void k_neg_offdiag(double2 *Bblk, double2 *Cblk, long long ld, const double2 *V, int h) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -229,7 +236,9 @@ void zgemm(apf_ctx *c, bool ta, bool tb, int M, int N, int K, double2 alpha, con
 // confined to the diagonal leaf blocks.
 void invert_sym64(apf_ctx *c, double2 *X, int n, long long ld, double2 *scr1, double2 *scr2, cudaStream_t s) {
     if (n <= LEAF64) {
-        APF_LAUNCH(c, k_leaf_inv64, 1, 256, n * n * (int)sizeof(double2), s, X, n, ld, c->d_flags);
+        if (n == 32) APF_LAUNCH(c, k_leaf64<32>, 1, 128, leaf_smem_bytes<32>(16), s, X, ld, c->d_flags);
+        else if (n == 16) APF_LAUNCH(c, k_leaf64<16>, 1, 64, leaf_smem_bytes<16>(16), s, X, ld, c->d_flags);
+        else APF_LAUNCH(c, k_leaf_inv64, 1, 256, n * n * (int)sizeof(double2), s, X, n, ld, c->d_flags);
         return;
     }
     int h = n / 2;

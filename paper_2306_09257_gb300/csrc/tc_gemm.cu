@@ -323,8 +323,18 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
     if (!make_map(&ma, A, BM) || !make_map(&mb, B, bn))
         return set_err(c, APF_ECUDA, "tensor map encode failed (M=%d N=%d kp=%lld)", M, N, A.kp);
     dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM);
+    int pi = -1;
+    if (c->prof_on && 2 * (c->prof_used + 1) <= (int)c->prof_ev.size()) {
+        pi = c->prof_used++;
+        // complex m x k x n product: M = m, N = 2n, kp ~ 2k real
+        double alg = 2.0 * (double)M * (double)N * (double)A.kp;
+        c->prof_alg[pi] = alg;
+        c->prof_hw[pi] = alg * p.nseg;
+        cudaEventRecord(c->prof_ev[2 * pi], s);
+    }
     constexpr int smem_wide = Layout<256, 4>::TOTAL, smem_narrow = Layout<128, 6>::TOTAL;
     if (wide) APF_LAUNCH(c, (k_tc_gemm<256, 4>), grid, 192, smem_wide, s, ma, mb, p);
     else APF_LAUNCH(c, (k_tc_gemm<128, 6>), grid, 192, smem_narrow, s, ma, mb, p);
+    if (pi >= 0) cudaEventRecord(c->prof_ev[2 * pi + 1], s);
     return APF_OK;
 }
