@@ -54,6 +54,7 @@ static bool is_device_ptr(const void *p) {
 }
 
 static void free_workspace(apf_ctx *c) {
+    graphs_reset(c);
     mixed_free(c);
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
@@ -152,8 +153,14 @@ int apf_create(apf_ctx **out, int cuda_device, int precision) {
     c->device = cuda_device;
     c->precision = precision;
     for (auto &ev : c->ev) cudaEventCreate(&ev);
+    cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     slab64_init_attrs();
+    boundary_init_attrs();
     mixed_init_attrs();
+    if (precision != APF_FP64 && tc_init() != APF_OK) {
+        apf_destroy(c);
+        return set_err(nullptr, APF_ECUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+    }
     *out = c;
     return APF_OK;
 }
@@ -165,6 +172,8 @@ void apf_destroy(apf_ctx *c) {
     free_workspace(c);
     if (c->d_eps) cudaFree(c->d_eps);
     for (auto &ev : c->ev) if (ev) cudaEventDestroy(ev);
+    for (auto &ev : c->prof_ev) if (ev) cudaEventDestroy(ev);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -187,6 +196,7 @@ int apf_set_grid(apf_ctx *c, int nx, int ny, int npml_bot, int npml_top, double 
     c->grid_set = true;
     c->eps_set = false;
     c->ch_set = false;
+    graphs_reset(c);
     return APF_OK;
 }
 
@@ -226,6 +236,7 @@ int apf_set_eps(apf_ctx *c, const double *eps_slab, int j0, int h, double eps_su
         if (e != cudaSuccess) return check_cuda(c, e, "upload eps");
     }
     bool changed = (c->h != h) || (c->eps_sub != eps_sub) || (c->eps_clad != eps_clad);
+    if (changed || c->j0 != j0) graphs_reset(c);
     c->h = h; c->j0 = j0; c->eps_sub = eps_sub; c->eps_clad = eps_clad;
     c->eps_set = true;
     if (changed) c->ch_set = false;
@@ -256,6 +267,7 @@ int apf_set_channels(apf_ctx *c, const int *m_in, int n_in, const int *m_out, in
     c->m_in = vin;
     c->m_out = vout;
     c->ch_set = true;
+    graphs_reset(c);
     cudaSetDevice(c->device);
     int rc = ensure_workspace(c);
     if (rc != APF_OK) { c->ch_set = false; return rc; }
@@ -288,7 +300,7 @@ int apf_set_profiling(apf_ctx *c, int enable) {
     if (!c) return APF_EINVAL;
     cudaSetDevice(c->device);
     c->prof = apf_profile{};
-    c->prof_used = 0;
+    if ((enable != 0) != c->prof_on) graphs_reset(c);
     c->prof_on = enable != 0;
     if (c->prof_on && c->prof_ev.empty()) {
         const int pairs = 16384;
@@ -337,19 +349,15 @@ static void fields64(apf_ctx *c, cudaStream_t s) {
     }
 }
 
-static int run_solve(apf_ctx *c, cudaStream_t s) {
-    if (!c->grid_set || !c->eps_set || !c->ch_set)
-        return set_err(c, APF_ESTATE, "solve needs apf_set_grid, apf_set_eps and apf_set_channels");
-    cudaSetDevice(c->device);
+// Everything up to the first host synchronization: boundary elimination, slab
+// elimination and the first field sweep.  Captured once into a CUDA graph.
+static int main_body(apf_ctx *c, cudaStream_t s) {
     int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
     long long nx = c->nx, L = (long long)ncol * nx;
-    c->launches = 0;
-    c->stats.refine_iters = 0;
-    c->stats.residual = 0.0;
     cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), s);
-    cudaEventRecord(c->ev[0], s);
+    record_event(c, c->ev[0], s);
     launch_boundary(c, s);
-    cudaEventRecord(c->ev[1], s);
+    record_event(c, c->ev[1], s);
     int rc = APF_OK;
     if (c->precision == APF_FP64) {
         long long nn = nx * nx;
@@ -362,12 +370,26 @@ static int run_solve(apf_ctx *c, cudaStream_t s) {
         rc = mixed_eliminate(c, s);
         if (rc != APF_OK) return rc;
     }
-    cudaEventRecord(c->ev[2], s);
+    record_event(c, c->ev[2], s);
     launch_zero(c, c->d_E, sizeof(double2) * c->h * L, s);
     launch_build_rhs(c, c->d_E, s);
     if (c->precision == APF_FP64) fields64(c, s);
-    else {
-        rc = mixed_solve_fields(c, s);
+    else rc = mixed_fields_begin(c, s);
+    return rc;
+}
+
+static int run_solve(apf_ctx *c, cudaStream_t s) {
+    if (!c->grid_set || !c->eps_set || !c->ch_set)
+        return set_err(c, APF_ESTATE, "solve needs apf_set_grid, apf_set_eps and apf_set_channels");
+    cudaSetDevice(c->device);
+    c->launches = 0;
+    c->prof_used = c->prof_static;
+    c->stats.refine_iters = 0;
+    c->stats.residual = 0.0;
+    int rc = run_graph(c, c->g_main, s, main_body);
+    if (rc != APF_OK) return rc;
+    if (c->precision != APF_FP64) {
+        rc = mixed_refine(c, s);
         if (rc != APF_OK && rc != APF_ENOCONV) return rc;
     }
     cudaEventRecord(c->ev[3], s);
@@ -376,9 +398,68 @@ static int run_solve(apf_ctx *c, cudaStream_t s) {
     return rc;
 }
 
-// Fold the GEMM events of the finished solve into the profile totals.
-void prof_collect(apf_ctx *c) {
-    for (int i = 0; i < c->prof_used; ++i) {
+void record_event(apf_ctx *c, cudaEvent_t e, cudaStream_t s) {
+    if (c->capturing) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else cudaEventRecord(e, s);
+}
+
+void graphs_reset(apf_ctx *c) {
+    for (GraphSlot *g : {&c->g_main, &c->g_resid, &c->g_correct}) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        *g = GraphSlot{};
+    }
+    c->prof_static = 0;
+    c->prof_used = 0;
+}
+
+// Run `body` on stream s: the first time it is captured (on the context's
+// capture stream) into a graph, afterwards the graph is replayed.  If
+// capture is not possible the body runs eagerly.
+int run_graph(apf_ctx *c, GraphSlot &g, cudaStream_t s, int (*body)(apf_ctx *, cudaStream_t)) {
+    if (!c->use_graphs) return body(c, s);
+    if (!g.exec) {
+        long long l0 = c->launches;
+        int p0 = c->prof_used;
+        if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c->use_graphs = false;
+            return body(c, s);
+        }
+        c->capturing = true;
+        int rc = body(c, c->cap_stream);
+        c->capturing = false;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (rc != APF_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            c->launches = l0;
+            c->prof_used = p0;
+            return rc;
+        }
+        if (e != cudaSuccess || !graph || cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+            cudaGetLastError();
+            if (graph) cudaGraphDestroy(graph);
+            g.exec = nullptr;
+            c->use_graphs = false;
+            c->launches = l0;
+            c->prof_used = p0;
+            return body(c, s);
+        }
+        cudaGraphDestroy(graph);
+        g.launches = c->launches - l0;
+        c->launches = l0;
+        g.prof_lo = p0;
+        g.prof_hi = c->prof_used;
+        c->prof_static = c->prof_used;
+    }
+    cudaError_t e = cudaGraphLaunch(g.exec, s);
+    if (e != cudaSuccess) return check_cuda(c, e, "graph launch");
+    c->launches += g.launches;
+    return APF_OK;
+}
+
+void prof_collect_range(apf_ctx *c, int lo, int hi) {
+    for (int i = lo; i < hi; ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) == cudaSuccess) {
             c->prof.gemm_launches++;
@@ -388,7 +469,12 @@ void prof_collect(apf_ctx *c) {
         }
     }
     cudaGetLastError();
-    c->prof_used = 0;
+}
+
+// Fold the GEMM events of launches made outside graphs into the totals.
+void prof_collect(apf_ctx *c) {
+    prof_collect_range(c, c->prof_static, c->prof_used);
+    c->prof_used = c->prof_static;
 }
 
 static int finish(apf_ctx *c, cudaStream_t s, int rc_solve) {

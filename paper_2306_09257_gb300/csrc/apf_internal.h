@@ -52,8 +52,15 @@ struct GridDev {
 // Error flag bits written by kernels into ctx->d_flags[0].
 enum { FLAG_SINGULAR = 1, FLAG_NONFINITE = 2, FLAG_TIMEOUT = 4 };
 
-// Sizes of the mixed-mode (tensor-core) workspace; defined in tc_gemm.cu.
+// Sizes of the mixed-mode (tensor-core) workspace; defined in mixed.cu.
 struct MixedWork;
+
+// A captured CUDA graph for one phase of the solve.
+struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;  // kernels per replay
+    int prof_lo = 0, prof_hi = 0;  // profiling event pairs owned by this graph
+};
 
 struct apf_ctx {
     int device = 0;
@@ -97,7 +104,13 @@ struct apf_ctx {
     int *d_flags = nullptr;
     int *d_pairs = nullptr;      // objective (b, a) pairs
     MixedWork *mw = nullptr;
+    // CUDA graphs (captured on cap_stream, replayed on the caller's stream)
+    cudaStream_t cap_stream = nullptr;
+    bool use_graphs = true;
+    bool capturing = false;
+    GraphSlot g_main, g_resid, g_correct;
     // GEMM launch profiling
+    int prof_static = 0;  // pairs reserved by captured graphs
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;      // pairs
     std::vector<double> prof_alg, prof_hw; // per recorded pair
@@ -150,10 +163,17 @@ int mixed_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s);
 int mixed_alloc(apf_ctx *c);
 void mixed_free(apf_ctx *c);
 int mixed_eliminate(apf_ctx *c, cudaStream_t s);
-int mixed_solve_fields(apf_ctx *c, cudaStream_t s);
+int mixed_fields_begin(apf_ctx *c, cudaStream_t s);
+int mixed_refine(apf_ctx *c, cudaStream_t s);
 
 int set_err(apf_ctx *c, int code, const char *fmt, ...);
 void prof_collect(apf_ctx *c);
+void prof_collect_range(apf_ctx *c, int lo, int hi);
+void record_event(apf_ctx *c, cudaEvent_t e, cudaStream_t s);
+void graphs_reset(apf_ctx *c);
+int run_graph(apf_ctx *c, GraphSlot &g, cudaStream_t s, int (*body)(apf_ctx *, cudaStream_t));
+void boundary_init_attrs();
+int tc_init();
 void slab64_init_attrs();
 void mixed_init_attrs();
 int check_cuda(apf_ctx *c, cudaError_t e, const char *what);

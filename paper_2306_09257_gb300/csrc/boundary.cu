@@ -175,11 +175,6 @@ void launch_fft(apf_ctx *c, const double2 *in, double2 *out, int n, int batch, l
     int logn = 0;
     while ((1 << logn) < n) ++logn;
     int smem = fft_smem_bytes(n);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * (int)sizeof(double2));
-        attr_set = true;
-    }
     int threads = n / 2 < 256 ? n / 2 : 256;
     APF_LAUNCH(c, k_fft, batch, threads, smem, s, in, out, n, logn, in_stride, out_stride, sign, scale, c->d_tw);
 }
@@ -199,4 +194,8 @@ void launch_build_rhs(apf_ctx *c, double2 *E, cudaStream_t s) {
     int nin = (int)c->m_in.size(), nout = (int)c->m_out.size();
     dim3 grid((c->nx + 255) / 256, nin + nout);
     APF_LAUNCH(c, k_build_rhs, grid, 256, 0, s, g, c->d_min, nin, c->d_mout, nout, c->d_coef, E);
+}
+
+void boundary_init_attrs() {
+    cudaFuncSetAttribute(k_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * (int)sizeof(double2));
 }

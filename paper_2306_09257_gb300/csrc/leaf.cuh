@@ -142,3 +142,103 @@ template <int NB>
 constexpr int leaf_smem_bytes(int elem_bytes) {
     return NB * (NB + 4) * elem_bytes;
 }
+
+// Register-resident variant for the mixed path: thread t keeps row t/4,
+// columns sub + 4q (q < NB/4) of the block in registers; the pivot row is the
+// only data exchanged through shared memory.  Rows are never swapped: step k
+// takes the largest unused |a[r][k]| as pivot row p_k and eliminates column k
+// from every other row.  With piv[k] = p_k and ipiv[p_k] = k the inverse is
+// inv[ipiv[r]][piv[c]] = a[r][c] (written out by a scatter at the end).
+// For the non-pivot rows the update x[j] -= f * prow[j] also produces the
+// new column-k entry -f / pivot, because prow[k] holds 1 + 1/pivot there and
+// x[k] = f before the update.
+template <int NB>
+__device__ void leaf_gj_regs(float *re, float *im, long long ld, int *flags) {
+    constexpr int Q = NB / 4;
+    __shared__ float2 prow[NB];
+    __shared__ float mag[NB];
+    __shared__ int piv[NB], ipiv[NB];
+    __shared__ int s_p;
+    const int t = threadIdx.x, i = t >> 2, sub = t & 3, lane = t & 31;
+    float2 a[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        long long g = (long long)i * ld + sub + 4 * q;
+        a[q] = make_float2(re[g], im[g]);
+    }
+    bool used = false;
+    float2 col = a[0];  // column k value, valid on the owner lanes (sub == k % 4)
+    if (sub == 0) mag[i] = col.x * col.x + col.y * col.y;
+    __syncthreads();
+    for (int k = 0; k < NB; ++k) {
+        if (t < 32) {
+            float best = -1.f;
+            int bi = 0;
+#pragma unroll
+            for (int r0 = 0; r0 < NB; r0 += 32) {
+                float m = mag[r0 + t];
+                if (m > best) { best = m; bi = r0 + t; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                float ob = __shfl_down_sync(0xffffffffu, best, off);
+                int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (t == 0) {
+                s_p = bi;
+                piv[k] = bi;
+                ipiv[bi] = k;
+                if (!(best > 0.f) || !isfinite(best)) atomicOr(flags, FLAG_SINGULAR);
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        const float2 f = make_float2(__shfl_sync(0xffffffffu, col.x, (lane & ~3) | (k & 3)),
+                                     __shfl_sync(0xffffffffu, col.y, (lane & ~3) | (k & 3)));
+        float2 pinv;
+        {
+            float den = f.x * f.x + f.y * f.y;
+            pinv = make_float2(f.x / den, -f.y / den);
+        }
+        if (i == p) {
+            used = true;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int j = sub + 4 * q;
+                float2 x = (j == k) ? pinv
+                                    : make_float2(a[q].x * pinv.x - a[q].y * pinv.y, a[q].x * pinv.y + a[q].y * pinv.x);
+                a[q] = x;
+                prow[j] = (j == k) ? make_float2(1.f + pinv.x, pinv.y) : x;
+            }
+        }
+        __syncthreads();
+        float2 nc = make_float2(0.f, 0.f);
+        if (i != p) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int j = sub + 4 * q;
+                const float2 pr = prow[j];
+                float2 x = a[q];
+                x.x -= f.x * pr.x - f.y * pr.y;
+                x.y -= f.x * pr.y + f.y * pr.x;
+                a[q] = x;
+                if (j == k + 1) nc = x;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (sub + 4 * q == k + 1) nc = a[q];
+        }
+        col = nc;
+        if (k + 1 < NB && sub == ((k + 1) & 3)) mag[i] = used ? -1.f : nc.x * nc.x + nc.y * nc.y;
+        __syncthreads();
+    }
+    const int r = ipiv[i];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        long long g = (long long)r * ld + piv[sub + 4 * q];
+        re[g] = a[q].x;
+        im[g] = a[q].y;
+    }
+}

@@ -257,6 +257,11 @@ __global__ void __launch_bounds__(NB * 4) k_leaf32(float *re, float *im, long lo
     leaf_gj<float, NB, true>(io, flags);
 }
 
+template <int NB>
+__global__ void __launch_bounds__(NB * 4) k_leaf32r(float *re, float *im, long long ld, int *flags) {
+    leaf_gj_regs<NB>(re, im, ld, flags);
+}
+
 // C block <- -V, B block <- -V^T (planar float32).
 __global__ void k_negoff32(float *Bre, float *Bim, float *Cre, float *Cim, long long ld, const float *Vre,
                            const float *Vim, int h) {
@@ -457,9 +462,9 @@ int inv32(apf_ctx *c, const PV &X, int n, float *Tre, float *Tim, float *Vre, fl
     MixedWork *w = c->mw;
     if (n <= leaf_size(w)) {
         if (n == 128)
-            APF_LAUNCH(c, k_leaf32<128>, 1, 512, leaf_smem_bytes<128>(8), s, X.re, X.im, X.ld, c->d_flags);
+            APF_LAUNCH(c, k_leaf32r<128>, 1, 512, 0, s, X.re, X.im, X.ld, c->d_flags);
         else if (n == 64)
-            APF_LAUNCH(c, k_leaf32<64>, 1, 256, leaf_smem_bytes<64>(8), s, X.re, X.im, X.ld, c->d_flags);
+            APF_LAUNCH(c, k_leaf32r<64>, 1, 256, 0, s, X.re, X.im, X.ld, c->d_flags);
         else if (n == 32)
             APF_LAUNCH(c, k_leaf32<32>, 1, 128, leaf_smem_bytes<32>(8), s, X.re, X.im, X.ld, c->d_flags);
         else if (n == 16)
@@ -611,31 +616,58 @@ int mixed_eliminate(apf_ctx *c, cudaStream_t s) {
     return APF_OK;
 }
 
-int mixed_solve_fields(apf_ctx *c, cudaStream_t s) {
+// Right-hand side R (written into d_E by the caller), its column norms, and
+// the first low-precision solve E = Khat^-1 R.
+int mixed_fields_begin(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
     int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
-    long long L = (long long)ncol * c->nx, total = L * c->h;
-    // the right-hand side R (rows 0 and h-1 only) was written into d_E by the caller
+    long long total = (long long)ncol * c->nx * c->h;
     cudaMemcpyAsync(c->d_R, c->d_E, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s);
     APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, c->d_R, c->h, ncol, c->nx, w->rnorm);
-    int rc = approx_solve(c, c->d_R, c->d_E, nin, s);
+    return approx_solve(c, c->d_R, c->d_E, nin, s);
+}
+
+static int resid_body(apf_ctx *c, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    int ncol = (int)(c->m_in.size() + c->m_out.size());
+    residual(c, c->d_E, w->r, s);
+    APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, c->nx, w->rnorm + ncol);
+    return APF_OK;
+}
+
+static int correct_body(apf_ctx *c, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    int ncol = (int)(c->m_in.size() + c->m_out.size());
+    long long total = (long long)ncol * c->nx * c->h;
+    int rc = approx_solve(c, w->r, w->delta, ncol, s);
     if (rc) return rc;
+    APF_LAUNCH(c, k_axpy, (unsigned)((total + 255) / 256), 256, 0, s, c->d_E, w->delta, total);
+    return APF_OK;
+}
+
+// Float64 iterative refinement: r = R - K E, E += Khat^-1 r until
+// max_c ||r_c|| / ||R_c|| <= tol (or max_iters corrections).
+int mixed_refine(apf_ctx *c, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    int ncol = (int)(c->m_in.size() + c->m_out.size());
     std::vector<double> nr(ncol), ne(ncol);
-    int iters = 0;
+    int iters = 0, rc;
     double ratio = 0.0;
     for (;;) {
-        residual(c, c->d_E, w->r, s);
-        APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, c->nx, w->rnorm + ncol);
-        if (iters == 0) cudaMemcpyAsync(nr.data(), w->rnorm, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
+        if ((rc = run_graph(c, c->g_resid, s, resid_body))) return rc;
+        cudaMemcpyAsync(nr.data(), w->rnorm, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(ne.data(), w->rnorm + ncol, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return check_cuda(c, e, "refinement");
+        if (c->prof_on) {
+            const GraphSlot &g = iters == 0 ? c->g_main : c->g_correct;
+            prof_collect_range(c, g.prof_lo, g.prof_hi);
+        }
         ratio = 0.0;
         for (int i = 0; i < ncol; ++i) ratio = std::max(ratio, sqrt(ne[i] / std::max(nr[i], 1e-300)));
         if (!(ratio == ratio)) { ratio = INFINITY; break; }
         if (ratio <= c->ir_tol || iters >= c->ir_max) break;
-        if ((rc = approx_solve(c, w->r, w->delta, ncol, s))) return rc;
-        APF_LAUNCH(c, k_axpy, (unsigned)((total + 255) / 256), 256, 0, s, c->d_E, w->delta, total);
+        if ((rc = run_graph(c, c->g_correct, s, correct_body))) return rc;
         ++iters;
     }
     c->stats.refine_iters = iters;

@@ -301,6 +301,8 @@ void tc_init_attrs() {
     set_attr<128, 6>();
 }
 
+int tc_init() { return ensure_encode() ? APF_OK : APF_ECUDA; }
+
 int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M, int N, int n_cplx, float alpha,
             float beta, float *out_re, float *out_im, long long ldo, const float *in_re, const float *in_im,
             long long ldi, cudaStream_t s) {
@@ -330,11 +332,11 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
         double alg = 2.0 * (double)M * (double)N * (double)A.kp;
         c->prof_alg[pi] = alg;
         c->prof_hw[pi] = alg * p.nseg;
-        cudaEventRecord(c->prof_ev[2 * pi], s);
+        record_event(c, c->prof_ev[2 * pi], s);
     }
     constexpr int smem_wide = Layout<256, 4>::TOTAL, smem_narrow = Layout<128, 6>::TOTAL;
     if (wide) APF_LAUNCH(c, (k_tc_gemm<256, 4>), grid, 192, smem_wide, s, ma, mb, p);
     else APF_LAUNCH(c, (k_tc_gemm<128, 6>), grid, 192, smem_narrow, s, ma, mb, p);
-    if (pi >= 0) cudaEventRecord(c->prof_ev[2 * pi + 1], s);
+    if (pi >= 0) record_event(c, c->prof_ev[2 * pi + 1], s);
     return APF_OK;
 }
