@@ -155,6 +155,36 @@ typedef struct {
 int apf_set_profiling(apf_ctx *ctx, int enable);
 int apf_get_profile(const apf_ctx *ctx, apf_profile *prof);
 
+/* Allocation-free solve for small grids (the paper has no counterpart; it
+   exists for callers, not for the method).
+   Some callers cannot allocate device memory: code that runs under another
+   framework's memory pool, where a direct cudaMalloc would fail or steal
+   memory the pool counts on; code with a fixed device-memory budget; code in
+   a timing-critical loop, where cudaMalloc's implicit device-wide
+   synchronization is not acceptable.  apf_create and the apf_set_* calls
+   allocate, so such callers use this one context-free call instead.  It
+   computes the same S as apf_create(APF_FP64) + apf_set_grid + apf_set_eps +
+   apf_set_channels + apf_solve_S, with the same argument meanings
+   (eps_slab: h*nx float64, host or device; m_in / m_out: host int arrays or
+   NULL for the default channels; S: n_out*n_in complex128, host or device),
+   for nx <= 64 (a power of two), h <= 16 and n_in + n_out <= 128; larger
+   problems get APF_EINVAL and a message from apf_last_error(NULL).
+   All intermediate arrays live in one file-scope device array of
+   APF_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library
+   holds until the process exits; the call itself never allocates or frees
+   device memory.  The first call on a device looks up that array's device
+   address (once per device, with the device current); make that first call
+   before any stream capture.  The call runs on the current device, enqueues
+   on `stream` and synchronizes it before returning.  Every call shares the
+   one array and leaves its contents behind (each call zeroes what must start
+   at zero), so calls whose GPU work overlaps -- from two host threads or two
+   streams at once -- race on it and must be serialized by the caller. */
+#define APF_NOALLOC_SCRATCH_BYTES (4u << 20)
+int apf_solve_S_noalloc(int nx, int ny, int npml_bot, int npml_top, double lambda_px,
+                        const apf_pml_params *pml, const double *eps_slab, int j0, int h,
+                        double eps_sub, double eps_clad, const int *m_in, int n_in,
+                        const int *m_out, int n_out, double *S, void *stream);
+
 /* Message of the most recent failure on this context (or of apf_create when
    ctx is NULL).  Never NULL. */
 const char *apf_last_error(const apf_ctx *ctx);

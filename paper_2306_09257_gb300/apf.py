@@ -28,7 +28,7 @@ OBJECTIVES = {"power": APF_OBJ_POWER, "splitter": APF_OBJ_SPLITTER}
 EXPORTS = ("apf_create", "apf_destroy", "apf_set_grid", "apf_set_eps", "apf_set_channels",
            "apf_get_channels", "apf_solve_S", "apf_solve_S_grad", "apf_grad_from_gamma",
            "apf_set_refinement", "apf_get_stats", "apf_set_profiling", "apf_get_profile",
-           "apf_last_error", "apf_version")
+           "apf_solve_S_noalloc", "apf_last_error", "apf_version")
 
 
 class APFError(RuntimeError):
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.apf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     L.apf_set_profiling.argtypes = [vp, i]
     L.apf_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
+    L.apf_solve_S_noalloc.argtypes = [i, i, i, i, d, ctypes.POINTER(PML), dp, i, i, d, d, ip, i, ip, i, dp, vp]
     L.apf_last_error.argtypes = [vp]
     L.apf_last_error.restype = ctypes.c_char_p
     L.apf_version.argtypes = []

@@ -13,11 +13,12 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 
 
-static std::string g_create_err = "no error";
+static char g_create_err[512] = "no error";
 
 int set_err(apf_ctx *c, int code, const char *fmt, ...) {
     char buf[512];
@@ -25,7 +26,8 @@ int set_err(apf_ctx *c, int code, const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
-    if (c) c->err = buf; else g_create_err = buf;
+    if (c) c->err = buf;
+    else memcpy(g_create_err, buf, sizeof g_create_err);
     return code;
 }
 
@@ -84,7 +86,7 @@ static int dalloc(apf_ctx *c, T **p, size_t count) {
 
 // (Re)allocate the solve workspace when the problem size changed.  Solves never allocate.
 static int ensure_workspace(apf_ctx *c) {
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size();
+    int nin = c->nin, nout = c->nout;
     if (c->ws_nx == c->nx && c->ws_h == c->h && c->ws_min == nin && c->ws_mout == nout) return APF_OK;
     free_workspace(c);
     long long nx = c->nx, h = c->h, ncol = nin + nout;
@@ -177,7 +179,7 @@ void apf_destroy(apf_ctx *c) {
     delete c;
 }
 
-const char *apf_last_error(const apf_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+const char *apf_last_error(const apf_ctx *c) { return c ? c->err.c_str() : g_create_err; }
 
 int apf_set_grid(apf_ctx *c, int nx, int ny, int npml_bot, int npml_top, double lambda_px,
                  const apf_pml_params *pml) {
@@ -266,6 +268,8 @@ int apf_set_channels(apf_ctx *c, const int *m_in, int n_in, const int *m_out, in
     }
     c->m_in = vin;
     c->m_out = vout;
+    c->nin = (int)vin.size();
+    c->nout = (int)vout.size();
     c->ch_set = true;
     graphs_reset(c);
     cudaSetDevice(c->device);
@@ -280,8 +284,8 @@ int apf_set_channels(apf_ctx *c, const int *m_in, int n_in, const int *m_out, in
 int apf_get_channels(const apf_ctx *c, int *n_in, int *n_out, int *m_in, int *m_out) {
     if (!c) return APF_EINVAL;
     if (!c->ch_set) return APF_ESTATE;
-    if (n_in) *n_in = (int)c->m_in.size();
-    if (n_out) *n_out = (int)c->m_out.size();
+    if (n_in) *n_in = c->nin;
+    if (n_out) *n_out = c->nout;
     if (m_in) std::copy(c->m_in.begin(), c->m_in.end(), m_in);
     if (m_out) std::copy(c->m_out.begin(), c->m_out.end(), m_out);
     return APF_OK;
@@ -332,8 +336,8 @@ int apf_get_stats(const apf_ctx *c, apf_stats *st) {
 // ---------------------------------------------------------------------------
 // Solve pipeline
 // ---------------------------------------------------------------------------
-static void fields64(apf_ctx *c, cudaStream_t s) {
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+void fields64(apf_ctx *c, cudaStream_t s) {
+    int nin = c->nin, nout = c->nout, ncol = nin + nout;
     long long nx = c->nx, L = (long long)ncol * nx, nn = nx * nx;
     const double2 one = cmk(1, 0), zero = cmk(0, 0);
     // forward chain Y_j = G_{j-1} Y_{j-1} (input columns; Y_0 = R_0)
@@ -352,7 +356,7 @@ static void fields64(apf_ctx *c, cudaStream_t s) {
 // Everything up to the first host synchronization: boundary elimination, slab
 // elimination and the first field sweep.  Captured once into a CUDA graph.
 static int main_body(apf_ctx *c, cudaStream_t s) {
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    int nin = c->nin, nout = c->nout, ncol = nin + nout;
     long long nx = c->nx, L = (long long)ncol * nx;
     cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), s);
     record_event(c, c->ev[0], s);
@@ -513,7 +517,7 @@ int apf_solve_S(apf_ctx *c, double *S, void *stream) {
     int rc = run_solve(c, s);
     if (rc != APF_OK && rc != APF_ENOCONV) { cudaStreamSynchronize(s); return rc; }
     cudaEventRecord(c->ev[5], s);
-    size_t bytes = sizeof(double2) * c->m_in.size() * c->m_out.size();
+    size_t bytes = sizeof(double2) * (size_t)c->nin * c->nout;
     cudaMemcpyAsync(S, c->d_S, bytes, cudaMemcpyDefault, s);
     return finish(c, s, rc);
 }
@@ -537,7 +541,7 @@ int apf_solve_S_grad(apf_ctx *c, int objective, const double *params, int n_para
     rc2 = launch_gradient(c, c->d_Gam, s);
     if (rc2 != APF_OK) { cudaStreamSynchronize(s); return rc2; }
     cudaEventRecord(c->ev[5], s);
-    size_t sb = sizeof(double2) * c->m_in.size() * c->m_out.size();
+    size_t sb = sizeof(double2) * (size_t)c->nin * c->nout;
     if (S) cudaMemcpyAsync(S, c->d_S, sb, cudaMemcpyDefault, s);
     cudaMemcpyAsync(grad_eps, c->d_grad, sizeof(double) * c->h * c->nx, cudaMemcpyDefault, s);
     double fh = 0.0;
@@ -553,7 +557,7 @@ int apf_grad_from_gamma(apf_ctx *c, const double *Gamma, double *grad_eps, void 
     if (!c->ch_set || c->ws_nx < 0) return set_err(c, APF_ESTATE, "apf_grad_from_gamma needs a previous solve");
     cudaStream_t s = (cudaStream_t)stream;
     cudaSetDevice(c->device);
-    size_t sb = sizeof(double2) * c->m_in.size() * c->m_out.size();
+    size_t sb = sizeof(double2) * (size_t)c->nin * c->nout;
     cudaMemcpyAsync(c->d_Gam, Gamma, sb, cudaMemcpyDefault, s);
     c->launches = 0;
     cudaEventRecord(c->ev[4], s);

@@ -76,6 +76,7 @@ struct apf_ctx {
     // channels
     bool ch_set = false;
     std::vector<int> m_in, m_out;
+    int nin = 0, nout = 0;  // channel counts used by all device-side code
     // refinement
     double ir_tol = 1e-10;
     int ir_max = 8;
@@ -152,6 +153,8 @@ void invert_sym64(apf_ctx *c, double2 *X, int n, long long ld, double2 *scr1, do
 void launch_add(apf_ctx *c, double2 *T, const double2 *a, const double2 *b, long long n, cudaStream_t s);
 void launch_copy(apf_ctx *c, double2 *dst, const double2 *src, long long n, cudaStream_t s);
 void launch_zero(apf_ctx *c, void *dst, long long bytes, cudaStream_t s);
+
+void fields64(apf_ctx *c, cudaStream_t s);
 
 // readout.cu
 void launch_readout(apf_ctx *c, cudaStream_t s);  // S from fields

@@ -182,16 +182,16 @@ void launch_fft(apf_ctx *c, const double2 *in, double2 *out, int n, int batch, l
 void launch_boundary(apf_ctx *c, cudaStream_t s) {
     GridDev g = make_grid(c);
     APF_LAUNCH(c, k_boundary_sweep, (c->nx + 127) / 128, 128, 0, s, g, c->d_modes);
-    int nc = (int)(c->m_in.size() + c->m_out.size());
-    APF_LAUNCH(c, k_channel_coef, (nc + 127) / 128, 128, 0, s, g, c->d_min, (int)c->m_in.size(), c->d_mout,
-               (int)c->m_out.size(), c->d_modes, c->d_coef);
+    int nc = (c->nin + c->nout);
+    APF_LAUNCH(c, k_channel_coef, (nc + 127) / 128, 128, 0, s, g, c->d_min, c->nin, c->d_mout,
+               c->nout, c->d_modes, c->d_coef);
     // circulant generators: c(d) = (1/nx) sum_m sigma_m exp(2 pi i m d / nx)
     launch_fft(c, c->d_modes, c->d_circ, c->nx, 2, c->nx, c->nx, +1, 1.0 / c->nx, s);
 }
 
 void launch_build_rhs(apf_ctx *c, double2 *E, cudaStream_t s) {
     GridDev g = make_grid(c);
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size();
+    int nin = c->nin, nout = c->nout;
     dim3 grid((c->nx + 255) / 256, nin + nout);
     APF_LAUNCH(c, k_build_rhs, grid, 256, 0, s, g, c->d_min, nin, c->d_mout, nout, c->d_coef, E);
 }

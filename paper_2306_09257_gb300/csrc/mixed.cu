@@ -505,7 +505,7 @@ int inv32(apf_ctx *c, const PV &X, int n, float *Tre, float *Tim, float *Vre, fl
 // substitution).  mcols: columns that the forward sweep must carry.
 int approx_solve(apf_ctx *c, const double2 *Rin, double2 *Eout, int mcols, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    int nin = c->nin, nout = c->nout, ncol = nin + nout;
     int nx = c->nx, ns = w->nsplit_elim;
     long long L = (long long)ncol * nx;
     float *Ore = w->O32, *Oim = w->O32 + L;
@@ -534,7 +534,7 @@ int approx_solve(apf_ctx *c, const double2 *Rin, double2 *Eout, int mcols, cudaS
 
 int residual(apf_ctx *c, const double2 *E, double2 *r, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    int nin = c->nin, nout = c->nout, ncol = nin + nout;
     int nx = c->nx;
     long long L = (long long)ncol * nx;
     int logn = 0;
@@ -572,7 +572,7 @@ int mixed_alloc(apf_ctx *c) {
     MixedWork *w = new MixedWork();
     c->mw = w;
     long long n = c->nx, h = c->h;
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size();
+    int nin = c->nin, nout = c->nout;
     long long ncol = nin + nout;
     int rc;
 #define WA(p, cnt) if ((rc = walloc(c, w, &(p), (cnt))) != APF_OK) return rc;
@@ -620,7 +620,7 @@ int mixed_eliminate(apf_ctx *c, cudaStream_t s) {
 // the first low-precision solve E = Khat^-1 R.
 int mixed_fields_begin(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    int nin = c->nin, nout = c->nout, ncol = nin + nout;
     long long total = (long long)ncol * c->nx * c->h;
     cudaMemcpyAsync(c->d_R, c->d_E, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s);
     APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, c->d_R, c->h, ncol, c->nx, w->rnorm);
@@ -629,7 +629,7 @@ int mixed_fields_begin(apf_ctx *c, cudaStream_t s) {
 
 static int resid_body(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int ncol = (int)(c->m_in.size() + c->m_out.size());
+    int ncol = (c->nin + c->nout);
     residual(c, c->d_E, w->r, s);
     APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, c->nx, w->rnorm + ncol);
     return APF_OK;
@@ -637,7 +637,7 @@ static int resid_body(apf_ctx *c, cudaStream_t s) {
 
 static int correct_body(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int ncol = (int)(c->m_in.size() + c->m_out.size());
+    int ncol = (c->nin + c->nout);
     long long total = (long long)ncol * c->nx * c->h;
     int rc = approx_solve(c, w->r, w->delta, ncol, s);
     if (rc) return rc;
@@ -649,7 +649,7 @@ static int correct_body(apf_ctx *c, cudaStream_t s) {
 // max_c ||r_c|| / ||R_c|| <= tol (or max_iters corrections).
 int mixed_refine(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int ncol = (int)(c->m_in.size() + c->m_out.size());
+    int ncol = (c->nin + c->nout);
     std::vector<double> nr(ncol), ne(ncol);
     int iters = 0, rc;
     double ratio = 0.0;
@@ -679,7 +679,7 @@ int mixed_refine(apf_ctx *c, cudaStream_t s) {
 // g_j(x) = 2 k^2 Re sum_b Phi_j[b][x] Q_j[b][x] in float64.
 int mixed_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    int nin = c->nin, nout = c->nout, ncol = nin + nout;
     int nx = c->nx, ns = w->nsplit_grad;
     long long L = (long long)ncol * nx;
     PackView pa = pack64A(c, w->PA, Gamma, nullptr, nin, nout, nin, ns, s);

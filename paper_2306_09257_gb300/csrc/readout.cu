@@ -85,7 +85,7 @@ __global__ void k_grad_rowdot(const double2 *E, const double2 *Q, int h, int nx,
 }  // namespace
 
 void launch_readout(apf_ctx *c, cudaStream_t s) {
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    int nin = c->nin, nout = c->nout, ncol = nin + nout;
     const double2 *Eh = c->d_E + (long long)(c->h - 1) * ncol * c->nx;
     launch_fft(c, Eh, c->d_fft, c->nx, nin, c->nx, c->nx, -1, 1.0 / sqrt((double)c->nx), s);
     dim3 grid((nin + 127) / 128, nout);
@@ -106,7 +106,7 @@ int launch_objective(apf_ctx *c, int objective, const double *params, int n_para
         if (v != (double)(int)v) return set_err(c, APF_EINVAL, "objective order %g is not an integer", v);
         o.d[i] = (int)v;
     }
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size();
+    int nin = c->nin, nout = c->nout;
     cudaMemsetAsync(c->d_Gam, 0, sizeof(double2) * (size_t)nin * nout, s);
     APF_LAUNCH(c, k_objective, 1, 1024, 0, s, c->d_S, c->d_min, c->d_mout, nin, nout, o, objective, params[0],
                c->d_Gam, c->d_f);
@@ -115,7 +115,7 @@ int launch_objective(apf_ctx *c, int objective, const double *params, int n_para
 
 int launch_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s) {
     if (c->precision != APF_FP64) return mixed_gradient(c, Gamma, s);
-    int nin = (int)c->m_in.size(), nout = (int)c->m_out.size(), ncol = nin + nout;
+    int nin = c->nin, nout = c->nout, ncol = nin + nout;
     long long nx = c->nx;
     // Q_j = Gamma (n_out x n_in) * F_j (n_in x nx), batched over the slab rows
     zgemm(c, false, false, nout, c->nx, nin, cmk(1, 0), Gamma, nin, 0, c->d_E, nx, (long long)ncol * nx, cmk(0, 0),
