@@ -61,8 +61,8 @@ static void free_workspace(apf_ctx *c) {
     for (void *p : c->allocs) cudaFree(p);
     c->allocs.clear();
     c->ws_bytes = 0;
-    c->ws_nx = c->ws_h = c->ws_min = c->ws_mout = -1;
-    c->d_min = c->d_mout = nullptr; c->d_modes = c->d_coef = c->d_circ = c->d_tw = nullptr;
+    c->ws_nx = c->ws_ny = c->ws_h = c->ws_min = c->ws_mout = -1;
+    c->d_min = c->d_mout = nullptr; c->d_stretch = nullptr; c->d_modes = c->d_coef = c->d_circ = c->d_tw = nullptr;
     c->d_G = c->d_scr1 = c->d_scr2 = c->d_E = c->d_T = c->d_R = nullptr;
     c->d_S = c->d_Gam = c->d_Q = c->d_fft = nullptr;
     c->d_grad = c->d_f = c->d_colnorm = nullptr;
@@ -87,13 +87,14 @@ static int dalloc(apf_ctx *c, T **p, size_t count) {
 // (Re)allocate the solve workspace when the problem size changed.  Solves never allocate.
 static int ensure_workspace(apf_ctx *c) {
     int nin = c->nin, nout = c->nout;
-    if (c->ws_nx == c->nx && c->ws_h == c->h && c->ws_min == nin && c->ws_mout == nout) return APF_OK;
+    if (c->ws_nx == c->nx && c->ws_ny == c->ny && c->ws_h == c->h && c->ws_min == nin && c->ws_mout == nout)
+        return APF_OK;
     free_workspace(c);
     long long nx = c->nx, h = c->h, ncol = nin + nout;
     int rc;
 #define AL(p, n) if ((rc = dalloc(c, &(p), (size_t)(n))) != APF_OK) { free_workspace(c); return rc; }
     AL(c->d_min, nin); AL(c->d_mout, nout);
-    AL(c->d_modes, 4 * nx); AL(c->d_coef, ncol); AL(c->d_circ, 2 * nx); AL(c->d_tw, nx / 2);
+    AL(c->d_modes, 4 * nx); AL(c->d_stretch, 2 * (c->ny + 1)); AL(c->d_coef, ncol); AL(c->d_circ, 2 * nx); AL(c->d_tw, nx / 2);
     if (c->precision == APF_FP64) {
         AL(c->d_G, h * nx * nx);
         AL(c->d_scr1, nx * nx / 2); AL(c->d_scr2, nx * nx / 2);
@@ -113,7 +114,7 @@ static int ensure_workspace(apf_ctx *c) {
     launch_twiddles(c, 0);
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { free_workspace(c); return check_cuda(c, e, "twiddles"); }
-    c->ws_nx = c->nx; c->ws_h = c->h; c->ws_min = nin; c->ws_mout = nout;
+    c->ws_nx = c->nx; c->ws_ny = c->ny; c->ws_h = c->h; c->ws_min = nin; c->ws_mout = nout;
     return APF_OK;
 }
 

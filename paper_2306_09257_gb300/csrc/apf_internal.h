@@ -81,13 +81,14 @@ struct apf_ctx {
     double ir_tol = 1e-10;
     int ir_max = 8;
     // workspace signature
-    int ws_nx = -1, ws_h = -1, ws_min = -1, ws_mout = -1;
+    int ws_nx = -1, ws_ny = -1, ws_h = -1, ws_min = -1, ws_mout = -1;
     long long ws_bytes = 0;
     std::vector<void *> allocs;
     // device buffers (float64 path, also used by the mixed path)
     double *d_eps = nullptr;     // h*nx
     int *d_min = nullptr, *d_mout = nullptr;
     double2 *d_modes = nullptr;  // 4*nx: sigma_bot, sigma_top, fac_bot, tau
+    double2 *d_stretch = nullptr; // 2*(ny+1): s_j and 1/s_{j-1/2}
     double2 *d_coef = nullptr;   // n_in + n_out: beta_a, w_b
     double2 *d_circ = nullptr;   // 2*nx: circulant generators of Sigma_bot, Sigma_top
     double2 *d_tw = nullptr;     // nx/2 twiddles exp(-2 pi i k / nx)

@@ -32,41 +32,52 @@ __device__ double2 stretch_at(const GridDev &g, double y) {
     return cmk(1.0, alpha * pow(d / L, g.power));
 }
 
+// Stretch table: st[j] = s_j (integer rows), st[ny + 1 + j] = 1 / s_{j - 1/2}
+// for j = 0..ny (half-integer rows, Dirichlet walls beyond the ends).
+__global__ void k_stretch_table(GridDev g, double2 *st) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > g.ny) return;
+    if (j < g.ny) st[j] = stretch_at(g, (double)j);
+    st[g.ny + 1 + j] = cinv(stretch_at(g, j - 0.5));
+}
+
 // Diagonal of row j for Fourier order with eigenvalue lam of -d2/dx2:
 // s_j (lam - k^2 eps) + 1/s_{j+1/2} + 1/s_{j-1/2}.
-__device__ double2 row_diag(const GridDev &g, int j, double lam, double eps) {
-    double2 s = stretch_at(g, (double)j);
-    double2 t = cscale(s, lam - g.k * g.k * eps);
-    t = cadd(t, cinv(stretch_at(g, j + 0.5)));
-    t = cadd(t, cinv(stretch_at(g, j - 0.5)));
+__device__ __forceinline__ double2 row_diag(const GridDev &g, const double2 *st, int j, double lam, double eps) {
+    double2 t = cscale(st[j], lam - g.k * g.k * eps);
+    t = cadd(t, st[g.ny + 1 + j + 1]);
+    t = cadd(t, st[g.ny + 1 + j]);
     return t;
 }
 
-__global__ void k_boundary_sweep(GridDev g, double2 *modes) {
+__global__ void k_boundary_sweep(GridDev g, const double2 *st, double2 *modes) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= g.nx) return;
+    const double2 *ish = st + g.ny + 1;  // ish[j] = 1 / s_{j - 1/2}
     double sp = sinpi((double)m / (double)g.nx);
     double lam = 4.0 * sp * sp;
     // bottom: substrate + PML, rows 0 .. j0-1, eliminated upward
-    double2 dt = row_diag(g, 0, lam, g.eps_sub);
+    double2 dt = row_diag(g, st, 0, lam, g.eps_sub);
     double2 fac = cmk(1.0, 0.0);
     for (int j = 1; j < g.j0; ++j) {
-        double2 c = cinv(stretch_at(g, j - 0.5));
-        if (j - 1 >= g.jsrc) fac = cmul(fac, cdiv(c, dt));
-        dt = csub(row_diag(g, j, lam, g.eps_sub), cdiv(cmul(c, c), dt));
+        double2 c = ish[j];
+        double2 idt = cinv(dt);
+        if (j - 1 >= g.jsrc) fac = cmul(fac, cmul(c, idt));
+        dt = csub(row_diag(g, st, j, lam, g.eps_sub), cmul(cmul(c, c), idt));
     }
-    double2 c0 = cinv(stretch_at(g, g.j0 - 0.5));
-    fac = cmul(fac, cdiv(c0, dt));
-    double2 sig_bot = cscale(cdiv(cmul(c0, c0), dt), -1.0);
+    double2 c0 = ish[g.j0];
+    double2 idt0 = cinv(dt);
+    fac = cmul(fac, cmul(c0, idt0));
+    double2 sig_bot = cscale(cmul(cmul(c0, c0), idt0), -1.0);
     // top: cladding + PML, rows ny-1 .. j0+h, eliminated downward
-    double2 dd = row_diag(g, g.ny - 1, lam, g.eps_clad);
+    double2 dd = row_diag(g, st, g.ny - 1, lam, g.eps_clad);
     double2 tau = cmk(1.0, 0.0);
     for (int j = g.ny - 2; j >= g.j0 + g.h; --j) {
-        double2 c = cinv(stretch_at(g, j + 0.5));
-        dd = csub(row_diag(g, j, lam, g.eps_clad), cdiv(cmul(c, c), dd));
-        if (j <= g.jout) tau = cmul(tau, cdiv(cinv(stretch_at(g, j - 0.5)), dd));
+        double2 c = ish[j + 1];
+        dd = csub(row_diag(g, st, j, lam, g.eps_clad), cdiv(cmul(c, c), dd));
+        if (j <= g.jout) tau = cmul(tau, cdiv(ish[j], dd));
     }
-    double2 c1 = cinv(stretch_at(g, g.j0 + g.h - 0.5));
+    double2 c1 = ish[g.j0 + g.h];
     double2 sig_top = cscale(cdiv(cmul(c1, c1), dd), -1.0);
     modes[m] = sig_bot;
     modes[g.nx + m] = sig_top;
@@ -181,7 +192,8 @@ void launch_fft(apf_ctx *c, const double2 *in, double2 *out, int n, int batch, l
 
 void launch_boundary(apf_ctx *c, cudaStream_t s) {
     GridDev g = make_grid(c);
-    APF_LAUNCH(c, k_boundary_sweep, (c->nx + 127) / 128, 128, 0, s, g, c->d_modes);
+    APF_LAUNCH(c, k_stretch_table, (c->ny + 1 + 127) / 128, 128, 0, s, g, c->d_stretch);
+    APF_LAUNCH(c, k_boundary_sweep, (c->nx + 63) / 64, 64, 0, s, g, c->d_stretch, c->d_modes);
     int nc = (c->nin + c->nout);
     APF_LAUNCH(c, k_channel_coef, (nc + 127) / 128, 128, 0, s, g, c->d_min, c->nin, c->d_mout,
                c->nout, c->d_modes, c->d_coef);

@@ -242,3 +242,108 @@ __device__ void leaf_gj_regs(float *re, float *im, long long ld, int *flags) {
         im[g] = a[q].y;
     }
 }
+
+// Faster register-resident variant: two barriers per elimination step.
+//  * The argmax for the next pivot is reduced per warp during the update
+//    (by the lanes that own the next column) and finished redundantly by
+//    every thread from the per-warp partials.
+//  * The pivot row is published unscaled; each thread folds 1/pivot into its
+//    own row factor g = f / a_pk.  Column k of the published row carries
+//    a_pk + 1, so x[k] - g (a_pk + 1) = -g, the new column-k entry.
+template <int NB>
+__device__ void leaf_gj_regs2(float *re, float *im, long long ld, int *flags) {
+    constexpr int Q = NB / 4;
+    constexpr int NW = NB * 4 / 32;  // warps
+    __shared__ float2 prow[NB];
+    __shared__ float pmag[2][NW];
+    __shared__ int pidx[2][NW];
+    __shared__ int piv[NB], ipiv[NB];
+    const int t = threadIdx.x, i = t >> 2, sub = t & 3, lane = t & 31, warp = t >> 5;
+    float2 a[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        long long g = (long long)i * ld + sub + 4 * q;
+        a[q] = make_float2(re[g], im[g]);
+    }
+    bool used = false;
+    float2 col = a[0];
+    // warp-level partial argmax of |col|^2 over the owner lanes (sub == k % 4)
+    auto publish = [&](int k, int buf) {
+        float m = (sub == (k & 3) && !used) ? col.x * col.x + col.y * col.y : -1.f;
+        int idx = i;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            float om = __shfl_down_sync(0xffffffffu, m, off);
+            int oi = __shfl_down_sync(0xffffffffu, idx, off);
+            if (om > m || (om == m && oi < idx)) { m = om; idx = oi; }
+        }
+        if (lane == 0) { pmag[buf][warp] = m; pidx[buf][warp] = idx; }
+    };
+    publish(0, 0);
+    __syncthreads();
+    for (int k = 0; k < NB; ++k) {
+        const int buf = k & 1;
+        float best = -1.f;
+        int p = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            float m = pmag[buf][w];
+            int idx = pidx[buf][w];
+            if (m > best || (m == best && idx < p)) { best = m; p = idx; }
+        }
+        if (t == 0) {
+            piv[k] = p;
+            ipiv[p] = k;
+            if (!(best > 0.f) || !isfinite(best)) atomicOr(flags, FLAG_SINGULAR);
+        }
+        const float2 f = make_float2(__shfl_sync(0xffffffffu, col.x, (lane & ~3) | (k & 3)),
+                                     __shfl_sync(0xffffffffu, col.y, (lane & ~3) | (k & 3)));
+        if (i == p) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int j = sub + 4 * q;
+                prow[j] = (j == k) ? make_float2(a[q].x + 1.f, a[q].y) : a[q];
+            }
+        }
+        __syncthreads();
+        // pivot value from the published row (column k holds a_pk + 1)
+        const float2 pk = prow[k];
+        const float2 apk = make_float2(pk.x - 1.f, pk.y);
+        const float den = apk.x * apk.x + apk.y * apk.y;
+        const float2 pinv = make_float2(apk.x / den, -apk.y / den);
+        float2 nc = make_float2(0.f, 0.f);
+        if (i != p) {
+            const float2 g = make_float2(f.x * pinv.x - f.y * pinv.y, f.x * pinv.y + f.y * pinv.x);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int j = sub + 4 * q;
+                const float2 pr = prow[j];
+                float2 x = a[q];
+                x.x -= g.x * pr.x - g.y * pr.y;
+                x.y -= g.x * pr.y + g.y * pr.x;
+                a[q] = x;
+                if (j == k + 1) nc = x;
+            }
+        } else {
+            used = true;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int j = sub + 4 * q;
+                float2 x = (j == k) ? pinv
+                                    : make_float2(a[q].x * pinv.x - a[q].y * pinv.y, a[q].x * pinv.y + a[q].y * pinv.x);
+                a[q] = x;
+                if (j == k + 1) nc = x;
+            }
+        }
+        col = nc;
+        if (k + 1 < NB) publish(k + 1, buf ^ 1);
+        __syncthreads();
+    }
+    const int r = ipiv[i];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        long long g = (long long)r * ld + piv[sub + 4 * q];
+        re[g] = a[q].x;
+        im[g] = a[q].y;
+    }
+}

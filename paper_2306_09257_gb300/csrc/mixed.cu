@@ -50,37 +50,50 @@ __device__ __forceinline__ void split_bf16(float x, int nsplit, __nv_bfloat16 *o
 // layoutB = 0 (A operand): row r = [Re v(r,:), Im v(r,:)].
 // layoutB = 1 (B operand of C = A B, r indexing C's columns):
 //   row r = [Re v(r,:), -Im v(r,:)], row R + r = [Im v(r,:), Re v(r,:)].
-__global__ void k_pack32(const float *__restrict__ sre, const float *__restrict__ sim, long long ld, int R, int K,
-                         int trans, int layoutB, int nsplit, __nv_bfloat16 *out, long long kp,
-                         long long plane_pitch) {
+struct PackJob {
+    const float *re, *im;
+    long long ld;
+    int R, K, trans, layoutB, nsplit;
+    __nv_bfloat16 *out;
+    long long kp, plane_pitch;
+};
+struct PackJobs {
+    PackJob j[2];
+};
+
+__global__ void k_pack32(PackJobs jobs) {
+    const PackJob &J = jobs.j[blockIdx.z];
     __shared__ float tre[32][33], tim[32][33];
     int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    if (r0 >= J.R || k0 >= J.K) return;
     int tx = threadIdx.x, ty = threadIdx.y;
     for (int i = ty; i < 32; i += 8) {
-        if (!trans) {
+        if (!J.trans) {
             int r = r0 + i, k = k0 + tx;
             float a = 0.f, b = 0.f;
-            if (r < R && k < K) { a = sre[(long long)r * ld + k]; b = sim[(long long)r * ld + k]; }
+            if (r < J.R && k < J.K) { a = J.re[(long long)r * J.ld + k]; b = J.im[(long long)r * J.ld + k]; }
             tre[i][tx] = a; tim[i][tx] = b;
         } else {
             int k = k0 + i, r = r0 + tx;
             float a = 0.f, b = 0.f;
-            if (r < R && k < K) { a = sre[(long long)k * ld + r]; b = sim[(long long)k * ld + r]; }
+            if (r < J.R && k < J.K) { a = J.re[(long long)k * J.ld + r]; b = J.im[(long long)k * J.ld + r]; }
             tre[tx][i] = a; tim[tx][i] = b;
         }
     }
     __syncthreads();
+    const int R = J.R, K = J.K;
+    const long long kp = J.kp;
     for (int i = ty; i < 32; i += 8) {
         int r = r0 + i, k = k0 + tx;
         if (r >= R || k >= K) continue;
         float a = tre[i][tx], b = tim[i][tx];
         __nv_bfloat16 sa[3], sb[3], nb[3];
-        split_bf16(a, nsplit, sa);
-        split_bf16(b, nsplit, sb);
-        for (int p = 0; p < nsplit; ++p) nb[p] = __hneg(sb[p]);
-        for (int p = 0; p < nsplit; ++p) {
-            __nv_bfloat16 *o = out + p * plane_pitch;
-            if (!layoutB) {
+        split_bf16(a, J.nsplit, sa);
+        split_bf16(b, J.nsplit, sb);
+        for (int p = 0; p < J.nsplit; ++p) nb[p] = __hneg(sb[p]);
+        for (int p = 0; p < J.nsplit; ++p) {
+            __nv_bfloat16 *o = J.out + p * J.plane_pitch;
+            if (!J.layoutB) {
                 o[(long long)r * kp + k] = sa[p];
                 o[(long long)r * kp + K + k] = sb[p];
             } else {
@@ -259,7 +272,7 @@ __global__ void __launch_bounds__(NB * 4) k_leaf32(float *re, float *im, long lo
 
 template <int NB>
 __global__ void __launch_bounds__(NB * 4) k_leaf32r(float *re, float *im, long long ld, int *flags) {
-    leaf_gj_regs<NB>(re, im, ld, flags);
+    leaf_gj_regs2<NB>(re, im, ld, flags);
 }
 
 // C block <- -V, B block <- -V^T (planar float32).
@@ -424,15 +437,41 @@ struct PV {  // planar complex view
     PV off(long long r, long long c) const { return PV{re + r * ld + c, im + r * ld + c, ld}; }
 };
 
-PackView pack32(apf_ctx *c, __nv_bfloat16 *dst, const PV &src, int R, int K, bool trans, bool layoutB, int nsplit,
-                cudaStream_t s) {
+PackJob make_job(__nv_bfloat16 *dst, const PV &src, int R, int K, bool trans, bool layoutB, int nsplit,
+                 PackView *view) {
     long long kp = round_up(2LL * K, 64);
     long long rows = layoutB ? 2LL * R : R;
-    if (kp != 2LL * K) cudaMemsetAsync(dst, 0, sizeof(__nv_bfloat16) * rows * kp * nsplit, s);
-    dim3 grid((K + 31) / 32, (R + 31) / 32);
-    APF_LAUNCH(c, k_pack32, grid, dim3(32, 8), 0, s, src.re, src.im, src.ld, R, K, trans ? 1 : 0, layoutB ? 1 : 0,
-               nsplit, dst, kp, rows * kp);
-    return PackView{dst, rows, kp, nsplit, rows * kp};
+    *view = PackView{dst, rows, kp, nsplit, rows * kp};
+    return PackJob{src.re, src.im, src.ld, R, K, trans ? 1 : 0, layoutB ? 1 : 0, nsplit, dst, kp, rows * kp};
+}
+
+void launch_jobs(apf_ctx *c, const PackJob *js, int nj, cudaStream_t s) {
+    PackJobs jobs{};
+    int maxR = 0, maxK = 0;
+    for (int i = 0; i < nj; ++i) {
+        jobs.j[i] = js[i];
+        if (js[i].kp != 2LL * js[i].K)
+            cudaMemsetAsync(js[i].out, 0, sizeof(__nv_bfloat16) * (js[i].plane_pitch * js[i].nsplit), s);
+        maxR = std::max(maxR, js[i].R);
+        maxK = std::max(maxK, js[i].K);
+    }
+    dim3 grid((maxK + 31) / 32, (maxR + 31) / 32, nj);
+    APF_LAUNCH(c, k_pack32, grid, dim3(32, 8), 0, s, jobs);
+}
+
+PackView pack32(apf_ctx *c, __nv_bfloat16 *dst, const PV &src, int R, int K, bool trans, bool layoutB, int nsplit,
+                cudaStream_t s) {
+    PackView v;
+    PackJob j = make_job(dst, src, R, K, trans, layoutB, nsplit, &v);
+    launch_jobs(c, &j, 1, s);
+    return v;
+}
+
+// Pack the A and B operands of one product in a single launch.
+void pack2(apf_ctx *c, PackView *va, __nv_bfloat16 *da, const PV &sa, int Ra, int Ka, bool ta, PackView *vb,
+           __nv_bfloat16 *db, const PV &sb, int Rb, int Kb, bool tb, int nsplit, cudaStream_t s) {
+    PackJob js[2] = {make_job(da, sa, Ra, Ka, ta, false, nsplit, va), make_job(db, sb, Rb, Kb, tb, true, nsplit, vb)};
+    launch_jobs(c, js, 2, s);
 }
 
 PackView pack64A(apf_ctx *c, __nv_bfloat16 *dst, const double2 *s1, const double2 *s2, long long ld, int R, int K,
@@ -481,17 +520,15 @@ int inv32(apf_ctx *c, const PV &X, int n, float *Tre, float *Tim, float *Vre, fl
     int rc;
     if ((rc = inv32(c, A, h, Tre + hh, Tim + hh, Vre + hh, Vim + hh, s))) return rc;
     // T = C Ai
-    PackView pa = pack32(c, w->PA, C, h, h, false, false, ns, s);
-    PackView pb = pack32(c, w->PB, A, h, h, false, true, ns, s);
+    PackView pa, pb;
+    pack2(c, &pa, w->PA, C, h, h, false, &pb, w->PB, A, h, h, false, ns, s);
     if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, 1.f, 0.f, T.re, T.im, T.ld, nullptr, nullptr, 0, s))) return rc;
     // D = D - T B   (B-operand columns = rows of C)
-    pa = pack32(c, w->PA, T, h, h, false, false, ns, s);
-    pb = pack32(c, w->PB, C, h, h, false, true, ns, s);
+    pack2(c, &pa, w->PA, T, h, h, false, &pb, w->PB, C, h, h, false, ns, s);
     if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, -1.f, 1.f, D.re, D.im, D.ld, D.re, D.im, D.ld, s))) return rc;
     if ((rc = inv32(c, D, h, Tre + hh, Tim + hh, Vre + hh, Vim + hh, s))) return rc;
     // V = Si T
-    pa = pack32(c, w->PA, D, h, h, false, false, ns, s);
-    pb = pack32(c, w->PB, T, h, h, true, true, ns, s);
+    pack2(c, &pa, w->PA, D, h, h, false, &pb, w->PB, T, h, h, true, ns, s);
     if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, 1.f, 0.f, V.re, V.im, V.ld, nullptr, nullptr, 0, s))) return rc;
     // A = Ai + V^T T
     pa = pack32(c, w->PA, V, h, h, true, false, ns, s);

@@ -37,7 +37,8 @@ extern "C" int apf_solve_S_noalloc(int nx, int ny, int npml_bot, int npml_top, d
     // ---- argument checks (host, before any launch) ----
     if (nx < 8 || nx > kMaxNx || (nx & (nx - 1))) return fail(APF_EINVAL, "nx must be a power of two in [8, 64]");
     if (h < 1 || h > kMaxH) return fail(APF_EINVAL, "h must be in [1, 16]");
-    if (npml_bot < 1 || npml_top < 1 || ny < npml_bot + npml_top + 4) return fail(APF_EINVAL, "bad PML / ny");
+    if (npml_bot < 1 || npml_top < 1 || ny < npml_bot + npml_top + 4 || ny > 4096)
+        return fail(APF_EINVAL, "bad PML / ny (ny <= 4096)");
     if (!(lambda_px > 2.0) || !isfinite(lambda_px)) return fail(APF_EINVAL, "lambda_px must be > 2");
     if (!eps_slab || !S) return fail(APF_EINVAL, "eps_slab and S must not be NULL");
     if (!(eps_sub > 0.0 && eps_clad > 0.0 && eps_clad <= eps_sub && isfinite(eps_sub)))
@@ -123,6 +124,7 @@ extern "C" int apf_solve_S_noalloc(int nx, int ny, int npml_bot, int npml_top, d
     c.d_min = (int *)carve(sizeof(int) * kMaxCols);
     c.d_mout = (int *)carve(sizeof(int) * kMaxCols);
     c.d_modes = (double2 *)carve(sizeof(double2) * 4 * n);
+    c.d_stretch = (double2 *)carve(sizeof(double2) * 2 * (ny + 1));
     c.d_coef = (double2 *)carve(sizeof(double2) * ncol);
     c.d_circ = (double2 *)carve(sizeof(double2) * 2 * n);
     c.d_tw = (double2 *)carve(sizeof(double2) * n / 2);
