@@ -213,22 +213,31 @@ __device__ void leaf_gj_regs(float *re, float *im, long long ld, int *flags) {
             }
         }
         __syncthreads();
-        float2 nc = make_float2(0.f, 0.f);
         if (i != p) {
+            const float nfx = -f.x, fy = f.y;
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                const int j = sub + 4 * q;
-                const float2 pr = prow[j];
+                const float2 pr = prow[sub + 4 * q];
                 float2 x = a[q];
-                x.x -= f.x * pr.x - f.y * pr.y;
-                x.y -= f.x * pr.y + f.y * pr.x;
+                x.x = fmaf(nfx, pr.x, x.x);
+                x.x = fmaf(fy, pr.y, x.x);
+                x.y = fmaf(nfx, pr.y, x.y);
+                x.y = fmaf(-fy, pr.x, x.y);
                 a[q] = x;
-                if (j == k + 1) nc = x;
             }
-        } else {
-#pragma unroll
-            for (int q = 0; q < Q; ++q)
-                if (sub + 4 * q == k + 1) nc = a[q];
+        }
+        // next pivot column: a uniform switch on its register slot
+        float2 nc = make_float2(0.f, 0.f);
+        switch ((k + 1) >> 2) {
+#define APF_NC_CASE(Z) case Z: if (Z < Q) nc = a[Z < Q ? Z : 0]; break;
+            APF_NC_CASE(0) APF_NC_CASE(1) APF_NC_CASE(2) APF_NC_CASE(3) APF_NC_CASE(4) APF_NC_CASE(5)
+            APF_NC_CASE(6) APF_NC_CASE(7) APF_NC_CASE(8) APF_NC_CASE(9) APF_NC_CASE(10) APF_NC_CASE(11)
+            APF_NC_CASE(12) APF_NC_CASE(13) APF_NC_CASE(14) APF_NC_CASE(15) APF_NC_CASE(16) APF_NC_CASE(17)
+            APF_NC_CASE(18) APF_NC_CASE(19) APF_NC_CASE(20) APF_NC_CASE(21) APF_NC_CASE(22) APF_NC_CASE(23)
+            APF_NC_CASE(24) APF_NC_CASE(25) APF_NC_CASE(26) APF_NC_CASE(27) APF_NC_CASE(28) APF_NC_CASE(29)
+            APF_NC_CASE(30) APF_NC_CASE(31)
+#undef APF_NC_CASE
+            default: break;
         }
         col = nc;
         if (k + 1 < NB && sub == ((k + 1) & 3)) mag[i] = used ? -1.f : nc.x * nc.x + nc.y * nc.y;

@@ -17,7 +17,7 @@
 #include <vector>
 
 struct MixedWork {
-    int nsplit_elim = 2, nsplit_grad = 3, leaf = 128;
+    int nsplit_elim = 2, nsplit_grad = 3, leaf = 128, leaf_variant = 0;
     float *Xre = nullptr, *Xim = nullptr;            // n x n working block
     float *Tre = nullptr, *Tim = nullptr;            // recursion scratch (n*n/2 each)
     float *Vre = nullptr, *Vim = nullptr;
@@ -272,6 +272,11 @@ __global__ void __launch_bounds__(NB * 4) k_leaf32(float *re, float *im, long lo
 
 template <int NB>
 __global__ void __launch_bounds__(NB * 4) k_leaf32r(float *re, float *im, long long ld, int *flags) {
+    leaf_gj_regs<NB>(re, im, ld, flags);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(NB * 4) k_leaf32r2(float *re, float *im, long long ld, int *flags) {
     leaf_gj_regs2<NB>(re, im, ld, flags);
 }
 
@@ -500,8 +505,14 @@ int leaf_size(const MixedWork *w) { return w->leaf; }
 int inv32(apf_ctx *c, const PV &X, int n, float *Tre, float *Tim, float *Vre, float *Vim, cudaStream_t s) {
     MixedWork *w = c->mw;
     if (n <= leaf_size(w)) {
-        if (n == 128)
+        if (n == 128 && w->leaf_variant == 1)
+            APF_LAUNCH(c, k_leaf32r2<128>, 1, 512, 0, s, X.re, X.im, X.ld, c->d_flags);
+        else if (n == 128 && w->leaf_variant == 2)
+            APF_LAUNCH(c, k_leaf32<128>, 1, 512, leaf_smem_bytes<128>(8), s, X.re, X.im, X.ld, c->d_flags);
+        else if (n == 128)
             APF_LAUNCH(c, k_leaf32r<128>, 1, 512, 0, s, X.re, X.im, X.ld, c->d_flags);
+        else if (n == 64 && w->leaf_variant == 1)
+            APF_LAUNCH(c, k_leaf32r2<64>, 1, 256, 0, s, X.re, X.im, X.ld, c->d_flags);
         else if (n == 64)
             APF_LAUNCH(c, k_leaf32r<64>, 1, 256, 0, s, X.re, X.im, X.ld, c->d_flags);
         else if (n == 32)
@@ -768,12 +779,14 @@ extern "C" int apf_debug_cgemm(apf_ctx *c, int m, int n, int k, const float *Are
 extern "C" int apf_debug_inv32(apf_ctx *c, int n, float *re, float *im, int leaf) {
     if (!c || !c->mw || n < 1 || n > c->nx || (n & (n - 1))) return APF_EINVAL;
     cudaSetDevice(c->device);
-    int old = c->mw->leaf;
-    if (leaf > 0) c->mw->leaf = leaf;
+    int old = c->mw->leaf, oldv = c->mw->leaf_variant;
+    // leaf = block size + 1000 * kernel variant (test and tuning hook)
+    if (leaf > 0) { c->mw->leaf = leaf % 1000; c->mw->leaf_variant = leaf / 1000; }
     cudaMemset(c->d_flags, 0, 16);
     int rc = inv32(c, PV{re, im, n}, n, c->mw->Tre, c->mw->Tim, c->mw->Vre, c->mw->Vim, 0);
     cudaError_t e = cudaDeviceSynchronize();
     c->mw->leaf = old;
+    c->mw->leaf_variant = oldv;
     if (rc) return rc;
     if (e != cudaSuccess) return check_cuda(c, e, "debug inv32");
     int fl = 0;
