@@ -61,46 +61,66 @@ struct PackJobs {
     PackJob j[2];
 };
 
-__global__ void k_pack32(PackJobs jobs) {
+// Tile: 32 rows x 64 k; thread (tx, ty) handles k = k0 + 2 tx, +1 (bf16x2 stores).
+__global__ void __launch_bounds__(256) k_pack32(PackJobs jobs) {
     const PackJob &J = jobs.j[blockIdx.z];
-    __shared__ float tre[32][33], tim[32][33];
-    int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    __shared__ float tre[32][65], tim[32][65];
+    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
     if (r0 >= J.R || k0 >= J.K) return;
-    int tx = threadIdx.x, ty = threadIdx.y;
-    for (int i = ty; i < 32; i += 8) {
-        if (!J.trans) {
-            int r = r0 + i, k = k0 + tx;
-            float a = 0.f, b = 0.f;
-            if (r < J.R && k < J.K) { a = J.re[(long long)r * J.ld + k]; b = J.im[(long long)r * J.ld + k]; }
-            tre[i][tx] = a; tim[i][tx] = b;
-        } else {
-            int k = k0 + i, r = r0 + tx;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (!J.trans) {
+        for (int i = ty; i < 32; i += 8) {
+            int r = r0 + i;
+            for (int kk = tx; kk < 64; kk += 32) {
+                int k = k0 + kk;
+                float a = 0.f, b = 0.f;
+                if (r < J.R && k < J.K) { a = J.re[(long long)r * J.ld + k]; b = J.im[(long long)r * J.ld + k]; }
+                tre[i][kk] = a; tim[i][kk] = b;
+            }
+        }
+    } else {
+        for (int kk = ty; kk < 64; kk += 8) {
+            int k = k0 + kk, r = r0 + tx;
             float a = 0.f, b = 0.f;
             if (r < J.R && k < J.K) { a = J.re[(long long)k * J.ld + r]; b = J.im[(long long)k * J.ld + r]; }
-            tre[tx][i] = a; tim[tx][i] = b;
+            tre[tx][kk] = a; tim[tx][kk] = b;
         }
     }
     __syncthreads();
-    const int R = J.R, K = J.K;
+    const int R = J.R, K = J.K, ns = J.nsplit;
     const long long kp = J.kp;
+    const int k = k0 + 2 * tx;
+    if (k >= K) return;
+    const bool two = (k + 1 < K);
     for (int i = ty; i < 32; i += 8) {
-        int r = r0 + i, k = k0 + tx;
-        if (r >= R || k >= K) continue;
-        float a = tre[i][tx], b = tim[i][tx];
-        __nv_bfloat16 sa[3], sb[3], nb[3];
-        split_bf16(a, J.nsplit, sa);
-        split_bf16(b, J.nsplit, sb);
-        for (int p = 0; p < J.nsplit; ++p) nb[p] = __hneg(sb[p]);
-        for (int p = 0; p < J.nsplit; ++p) {
+        int r = r0 + i;
+        if (r >= R) break;
+        __nv_bfloat16 a0[3], a1[3], b0[3], b1[3];
+        split_bf16(tre[i][2 * tx], ns, a0);
+        split_bf16(tim[i][2 * tx], ns, b0);
+        split_bf16(two ? tre[i][2 * tx + 1] : 0.f, ns, a1);
+        split_bf16(two ? tim[i][2 * tx + 1] : 0.f, ns, b1);
+        for (int p = 0; p < ns; ++p) {
             __nv_bfloat16 *o = J.out + p * J.plane_pitch;
+            __nv_bfloat162 re2 = __halves2bfloat162(a0[p], a1[p]);
+            __nv_bfloat162 im2 = __halves2bfloat162(b0[p], b1[p]);
+            __nv_bfloat162 nim2 = __halves2bfloat162(__hneg(b0[p]), __hneg(b1[p]));
+            auto st = [&](long long row, long long col, __nv_bfloat162 v) {
+                if (two && ((row * kp + col) & 1) == 0) {
+                    *reinterpret_cast<__nv_bfloat162 *>(o + row * kp + col) = v;
+                } else {
+                    o[row * kp + col] = v.x;
+                    if (two) o[row * kp + col + 1] = v.y;
+                }
+            };
             if (!J.layoutB) {
-                o[(long long)r * kp + k] = sa[p];
-                o[(long long)r * kp + K + k] = sb[p];
+                st(r, k, re2);
+                st(r, K + k, im2);
             } else {
-                o[(long long)r * kp + k] = sa[p];
-                o[(long long)r * kp + K + k] = nb[p];
-                o[(long long)(R + r) * kp + k] = sb[p];
-                o[(long long)(R + r) * kp + K + k] = sa[p];
+                st(r, k, re2);
+                st(r, K + k, nim2);
+                st(R + r, k, im2);
+                st(R + r, K + k, re2);
             }
         }
     }
@@ -160,22 +180,22 @@ __global__ void k_pack64_BT(const double2 *__restrict__ src, long long ld, int R
 // boundary circulants on the first / last slab row).
 __global__ void k_assemble32(GridDev g, int row, const double *eps, const double2 *circ, const float *Gre,
                              const float *Gim, float *Xre, float *Xim) {
-    int xp = blockIdx.x * blockDim.x + threadIdx.x;
-    int x = blockIdx.y;
-    int n = g.nx;
+    const int n = g.nx;
+    const int x = blockIdx.y;
+    const int xp = blockIdx.x * blockDim.x + threadIdx.x;
     if (xp >= n) return;
-    double vr = 0.0, vi = 0.0;
-    if (xp == x) vr += 4.0 - g.k * g.k * eps[(long long)row * n + x];
-    if (xp == (x + 1) % n) vr -= 1.0;
-    if (xp == (x + n - 1) % n) vr -= 1.0;
-    int d = (x - xp + n) % n;
-    if (row == 0) { vr += circ[d].x; vi += circ[d].y; }
-    if (row == g.h - 1) { vr += circ[n + d].x; vi += circ[n + d].y; }
-    long long idx = (long long)x * n + xp;
-    float fr = (float)vr, fi = (float)vi;
-    if (Gre) { fr -= Gre[idx]; fi -= Gim[idx]; }
-    Xre[idx] = fr;
-    Xim[idx] = fi;
+    float vr = 0.f, vi = 0.f;
+    if (xp == x) vr = (float)(4.0 - g.k * g.k * eps[(long long)row * n + x]);
+    const int dx = x - xp;
+    if (dx == 1 || dx == -1 || dx == n - 1 || dx == 1 - n) vr -= 1.f;
+    if (n == 2 && dx != 0) vr -= 1.f;  // both periodic neighbours coincide
+    const int d = dx < 0 ? dx + n : dx;
+    if (row == 0) { vr += (float)circ[d].x; vi += (float)circ[d].y; }
+    if (row == g.h - 1) { vr += (float)circ[n + d].x; vi += (float)circ[n + d].y; }
+    const long long idx = (long long)x * n + xp;
+    if (Gre) { vr -= Gre[idx]; vi -= Gim[idx]; }
+    Xre[idx] = vr;
+    Xim[idx] = vi;
 }
 
 // Float32 Gauss-Jordan inverse of an n x n (n <= 128) diagonal block with
@@ -460,7 +480,7 @@ void launch_jobs(apf_ctx *c, const PackJob *js, int nj, cudaStream_t s) {
         maxR = std::max(maxR, js[i].R);
         maxK = std::max(maxK, js[i].K);
     }
-    dim3 grid((maxK + 31) / 32, (maxR + 31) / 32, nj);
+    dim3 grid((maxK + 63) / 64, (maxR + 31) / 32, nj);
     APF_LAUNCH(c, k_pack32, grid, dim3(32, 8), 0, s, jobs);
 }
 

@@ -22,6 +22,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 namespace {
 
 constexpr int BM = 128;
@@ -117,15 +119,65 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 template <int BN, int STAGES>
 struct Layout {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int BAR = STAGES * STAGE;
-    static constexpr int TOTAL = BAR + (2 * STAGES + 1) * 8 + 16 + 1024;
+    static constexpr int TOTAL = BAR + (2 * STAGES + 4) * 8 + 16 + 1024;
 };
 
+// Epilogue of one 32-column chunk of one accumulator row.
+__device__ __forceinline__ void store_chunk(const TcParams &p, int row, int col0, const uint32_t (&r)[32]) {
+    if (row >= p.M) return;
+    const bool use_beta = (p.beta != 0.0f);
+    float *op;
+    const float *ip;
+    int cc0;
+    if (col0 < p.n_cplx) { op = p.out_re; ip = p.in_re; cc0 = col0; }
+    else { op = p.out_im; ip = p.in_im; cc0 = col0 - p.n_cplx; }
+    const bool whole = (col0 + 32 <= p.N) && ((col0 < p.n_cplx) == (col0 + 31 < p.n_cplx));
+    float *dst = op + (long long)row * p.ldo + cc0;
+    const float *src = ip + (long long)row * p.ldi + cc0;
+    if (whole && ((((uintptr_t)dst) | (use_beta ? (uintptr_t)src : 0)) & 15) == 0) {
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            float4 o;
+            o.x = p.alpha * __uint_as_float(r[4 * v + 0]);
+            o.y = p.alpha * __uint_as_float(r[4 * v + 1]);
+            o.z = p.alpha * __uint_as_float(r[4 * v + 2]);
+            o.w = p.alpha * __uint_as_float(r[4 * v + 3]);
+            if (use_beta) {
+                float4 c = *reinterpret_cast<const float4 *>(src + 4 * v);
+                o.x += p.beta * c.x; o.y += p.beta * c.y; o.z += p.beta * c.z; o.w += p.beta * c.w;
+            }
+            *reinterpret_cast<float4 *>(dst + 4 * v) = o;
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int col = col0 + i;
+        if (col >= p.N) break;
+        float *o2;
+        const float *i2;
+        int cc;
+        if (col < p.n_cplx) { o2 = p.out_re; i2 = p.in_re; cc = col; }
+        else { o2 = p.out_im; i2 = p.in_im; cc = col - p.n_cplx; }
+        float v = p.alpha * __uint_as_float(r[i]);
+        if (use_beta) v += p.beta * i2[(long long)row * p.ldi + cc];
+        o2[(long long)row * p.ldo + cc] = v;
+    }
+}
+
+// Persistent: one CTA per SM walks the output tiles (M index fastest, so the
+// CTAs working on one B panel run together); two tensor-memory accumulators
+// let the epilogue of one tile overlap the MMAs of the next.
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(192, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
@@ -134,12 +186,14 @@ __global__ void __launch_bounds__(192, 1)
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + L::BAR);
     uint64_t *empty = full + STAGES;
-    uint64_t *accb = empty + STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(accb + 1);
+    uint64_t *tfull = empty + STAGES;   // [2]
+    uint64_t *tempty = tfull + 2;       // [2]
+    uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int Mt = (p.M + BM - 1) / BM, Nt = (p.N + BN - 1) / BN;
+    const int ntiles = Mt * Nt;
     const int total = p.nseg * p.kblocks;
 
     if (threadIdx.x == 0) {
@@ -147,14 +201,17 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accb, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(BN)
+                     "r"(2 * BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -163,72 +220,76 @@ __global__ void __launch_bounds__(192, 1)
     fence_after();
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
-
     int issued = 0;
+
     if (warp == 0) {
         if (lane == 0) {
-            for (int it = 0; it < total; ++it) {
-                int s = it % STAGES, r = it / STAGES;
-                if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) { ok = false; break; }
-                int seg = it / p.kblocks, kb = it - seg * p.kblocks;
-                int pa = (p.seg_pairs >> (4 * seg + 2)) & 3, pb = (p.seg_pairs >> (4 * seg)) & 3;
-                uint8_t *sa = smem + s * L::STAGE;
-                uint8_t *sb = sa + L::A_BYTES;
-                mbar_expect_tx(&full[s], L::A_BYTES + L::B_BYTES);
-                tma_load_3d(sa, &tmA, &full[s], kb * BK, m0, pa);
-                tma_load_3d(sb, &tmB, &full[s], kb * BK, n0, pb);
-                issued = it + 1;
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int m0 = (tile % Mt) * BM, n0 = (tile / Mt) * BN;
+                for (int kk = 0; kk < total; ++kk, ++it) {
+                    const int s = it % STAGES, r = it / STAGES;
+                    if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    const int seg = kk / p.kblocks, kb = kk - seg * p.kblocks;
+                    const int pa = (p.seg_pairs >> (4 * seg + 2)) & 3, pb = (p.seg_pairs >> (4 * seg)) & 3;
+                    uint8_t *sa = smem + s * L::STAGE;
+                    uint8_t *sb = sa + L::A_BYTES;
+                    mbar_expect_tx(&full[s], L::A_BYTES + L::B_BYTES);
+                    tma_load_3d(sa, &tmA, &full[s], kb * BK, m0, pa);
+                    tma_load_3d(sb, &tmB, &full[s], kb * BK, n0, pb);
+                    issued = it + 1;
+                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                    ((uint32_t)(BM >> 4) << 24);
-            for (int it = 0; it < total; ++it) {
-                int s = it % STAGES, r = it / STAGES;
-                if (!mbar_wait(&full[s], r & 1, abort_flag)) { ok = false; break; }
+            int it = 0, tl = 0;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tl) {
+                const int b = tl & 1, u = tl >> 1;
+                if (!mbar_wait(&tempty[b], (u & 1) ^ 1, abort_flag)) { ok = false; break; }
                 fence_after();
-                uint32_t sa = smem_u32(smem + s * L::STAGE);
-                uint32_t sb = sa + L::A_BYTES;
+                const uint32_t acc = tmem + (uint32_t)(b * BN);
+                for (int kk = 0; kk < total; ++kk, ++it) {
+                    const int s = it % STAGES, r = it / STAGES;
+                    if (!mbar_wait(&full[s], r & 1, abort_flag)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t sa = smem_u32(smem + s * L::STAGE);
+                    const uint32_t sb = sa + L::A_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                    mma_bf16(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc,
-                             (it > 0 || kk > 0) ? 1u : 0u);
+                    for (int k4 = 0; k4 < BK / 16; ++k4)
+                        mma_bf16(acc, sw128_desc(sa + k4 * 32), sw128_desc(sb + k4 * 32), idesc,
+                                 (kk > 0 || k4 > 0) ? 1u : 0u);
+                    mma_commit(&empty[s]);
                 }
-                mma_commit(&empty[s]);
+                if (!ok) break;
+                mma_commit(&tfull[b]);
             }
-            mma_commit(accb);
-            // on failure, let the MMAs already issued drain before TMEM is freed
-            if (!ok) mbar_wait(accb, 0, abort_flag, true);
+            if (!ok) {
+                // let the MMAs already issued drain before TMEM is freed
+                mma_commit(&tfull[0]);
+                mbar_wait(&tfull[0], 0, abort_flag, true);
+            }
         }
     } else {
         const int q = warp & 3;  // TMEM lane quarter this warp may access
-        if (!mbar_wait(accb, 0, abort_flag)) {
-            ok = false;
-        } else {
+        int tl = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tl) {
+            const int b = tl & 1, u = tl >> 1;
+            if (!mbar_wait(&tfull[b], u & 1, abort_flag)) { ok = false; break; }
             fence_after();
+            const int m0 = (tile % Mt) * BM, n0 = (tile / Mt) * BN;
             const int row = m0 + 32 * q + lane;
-            const bool use_beta = (p.beta != 0.0f);
 #pragma unroll 1
             for (int c = 0; c < BN; c += 32) {
                 uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, r);
-                if (row < p.M) {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        int col = n0 + c + i;
-                        if (col >= p.N) break;
-                        float *op;
-                        const float *ip;
-                        int cc;
-                        if (col < p.n_cplx) { op = p.out_re; ip = p.in_re; cc = col; }
-                        else { op = p.out_im; ip = p.in_im; cc = col - p.n_cplx; }
-                        float v = p.alpha * __uint_as_float(r[i]);
-                        if (use_beta) v += p.beta * ip[(long long)row * p.ldi + cc];
-                        op[(long long)row * p.ldo + cc] = v;
-                    }
-                }
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + c), r);
+                store_chunk(p, row, n0 + c, r);
             }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
         }
     }
     if (!ok) {
@@ -245,7 +306,7 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     if (warp == 1) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
     }
 }
 
@@ -318,13 +379,25 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
     p.in_re = in_re ? in_re : out_re; p.in_im = in_im ? in_im : out_im; p.ldi = in_re ? ldi : ldo;
     p.flags = c->d_flags;
     CUtensorMap ma, mb;
-    // Wide tiles when they still fill the GPU; otherwise 128-wide tiles.
-    long long tiles256 = (long long)((N + 255) / 256) * ((M + BM - 1) / BM);
-    bool wide = (N > 128) && tiles256 >= 120;
+    // Tile width: score the wave utilisation of 256- and 128-wide tiles.
+    static int num_sms = 0;
+    if (!num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (num_sms <= 0) num_sms = 148;
+    }
+    auto util = [&](int bn) {
+        long long t = (long long)((N + bn - 1) / bn) * ((M + BM - 1) / BM);
+        long long waves = (t + num_sms - 1) / num_sms;
+        return (double)t / (double)(waves * num_sms);
+    };
+    bool wide = (N > 128) && util(256) >= 0.9 * util(128);
     int bn = wide ? 256 : 128;
     if (!make_map(&ma, A, BM) || !make_map(&mb, B, bn))
         return set_err(c, APF_ECUDA, "tensor map encode failed (M=%d N=%d kp=%lld)", M, N, A.kp);
-    dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM);
+    long long ntiles = (long long)((N + bn - 1) / bn) * ((M + BM - 1) / BM);
+    dim3 grid((unsigned)std::min<long long>(ntiles, num_sms));
     int pi = -1;
     if (c->prof_on && 2 * (c->prof_used + 1) <= (int)c->prof_ev.size()) {
         pi = c->prof_used++;
