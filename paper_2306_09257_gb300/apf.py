@@ -128,6 +128,7 @@ class Solver:
         self.precision = precision
         self.device = device
         self.nx = self.h = None
+        self.version = 0  # bumped by every call that changes the stored fields
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -157,6 +158,7 @@ class Solver:
         self._check(self._L.apf_set_eps(self._h, _ptr(eps_slab, np.float64), int(j0), h,
                                         float(eps_sub), float(eps_clad)))
         self.h = h
+        self.version += 1
 
     def set_channels(self, m_in: Optional[Sequence[int]] = None, m_out: Optional[Sequence[int]] = None):
         def arr(v):
@@ -186,6 +188,7 @@ class Solver:
     def solve_S(self, out=None, allow_noconv=False):
         S = self._alloc_S() if out is None else out
         st = _stream_of(S)
+        self.version += 1
         self._check(self._L.apf_solve_S(self._h, _ptr(S, np.complex128), st),
                     allow=(APF_ENOCONV,) if allow_noconv else ())
         return S
@@ -202,6 +205,7 @@ class Solver:
         oid, params, npar = self.objective_params(kind, orders, target)
         f = ctypes.c_double()
         st = _stream_of(S, g)
+        self.version += 1
         self._check(self._L.apf_solve_S_grad(self._h, oid, params, npar, _ptr(S, np.complex128),
                                              ctypes.byref(f), _ptr(g, np.float64), st),
                     allow=(APF_ENOCONV,) if allow_noconv else ())

@@ -1,0 +1,62 @@
+"""Gradient-descent optimisation of the slab permittivity with the
+backtracking (Armijo) line search of the paper's supplement (Sec. 4, Eq. S2):
+start from gamma_max, shrink by tau = 1/2 until
+    f(x_new) <= f(x) - c1 * ||x_new - x||^2 / gamma,    c1 = 1e-2,
+which is Eq. (S2) when no bound is active (x_new - x = -gamma grad f).  The
+permittivity is kept in [eps_lo, eps_hi] by projection.  Every trial point is
+one APF evaluation that returns f and grad f together, so the gradient of the
+accepted point is reused by the next iteration.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from typing import List, Sequence
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class History:
+    f: List[float]
+    evals: int
+    seconds: float
+    gammas: List[float]
+
+    @property
+    def iters_per_second(self) -> float:
+        return (len(self.f) - 1) / self.seconds if self.seconds > 0 else 0.0
+
+
+def optimize(solver, eps0: np.ndarray, eps_sub: float, eps_clad: float, j0: int, kind: str,
+             orders: Sequence[int], target: float, iters: int, gamma_max: float = None,
+             tau: float = 0.5, c1: float = 1e-2, eps_lo: float = 1.0, eps_hi: float = 2.25,
+             max_backtracks: int = 12):
+    eps = np.clip(np.asarray(eps0, np.float64).copy(), eps_lo, eps_hi)
+    t0 = time.perf_counter()
+    solver.set_eps(eps, eps_sub, eps_clad, j0=j0)
+    _, f, g = solver.solve_S_grad(kind, orders, target)
+    evals = 1
+    hist = History([f], 0, 0.0, [])
+    if gamma_max is None:
+        gamma_max = 0.25 / max(float(np.abs(g).max()), 1e-30)
+    for _ in range(iters):
+        gamma = gamma_max
+        accepted = False
+        for _ in range(max_backtracks):
+            trial = np.clip(eps - gamma * g, eps_lo, eps_hi)
+            solver.set_eps(trial, eps_sub, eps_clad, j0=j0)
+            _, ft, gt = solver.solve_S_grad(kind, orders, target)
+            evals += 1
+            if ft <= f - c1 * float(np.sum((trial - eps) ** 2)) / gamma:
+                eps, f, g = trial, ft, gt
+                accepted = True
+                break
+            gamma *= tau
+        hist.gammas.append(gamma if accepted else 0.0)
+        hist.f.append(f)
+        if not accepted:
+            break
+    hist.evals = evals
+    hist.seconds = time.perf_counter() - t0
+    return eps, hist
