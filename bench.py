@@ -29,6 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2306_09257_gb300 import replicas  # noqa: E402
 from paper_2306_09257_gb300 import workloads as W  # noqa: E402
 
 METRIC = "S+grad evals/s, mixed vs FP64 on 1 GB300 at stated err; % of tensor peak"
@@ -48,7 +49,7 @@ def args_parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--solves", type=int, default=4, help="oracle solves per CPU sample")
-    p.add_argument("--concurrent", type=int, default=8,
+    p.add_argument("--concurrent", type=int, default=4,
                    help="independent designs in flight per GPU (one context + stream + host thread each)")
     return p.parse_args()
 
@@ -208,7 +209,7 @@ def main():
     dev = torch.device("cuda", local)
     B = max(1, a.concurrent)
     nseeds = 4
-    eps_host = [[w.eps_slab(1000 * rank + 100 * b + i) for i in range(nseeds)] for b in range(B)]
+    eps_host = [[w.eps_slab(sd) for sd in row] for row in replicas.replica_seeds(rank, B, nseeds)]
     eps_dev = [[torch.tensor(e, device=dev) for e in row] for row in eps_host]
     solvers = [apf.solver_for_workload(w, eps_host[b][0], precision="mixed", device=local) for b in range(B)]
     s = solvers[0]
@@ -273,12 +274,8 @@ def main():
     prof = {k: sum(p[k] for p in profs) for k in profs[0]}
     for sv in solvers:
         sv.set_profiling(False)
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * B * a.steps / (ms / 1000.0)
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1))
+    value = replicas.whole_job_throughput(ws, B, a.steps, ms)
     launches = sum(x["launches"] for x in stats_acc)
     iters = stats_acc[0]["iters"]
     st_last = s.stats()
