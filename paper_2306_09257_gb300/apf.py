@@ -24,11 +24,13 @@ APF_OBJ_POWER, APF_OBJ_SPLITTER = 1, 2
 PRECISIONS = {"fp64": APF_FP64, "mixed": APF_MIXED_BF16X3, "bf16x3": APF_MIXED_BF16X3}
 OBJECTIVES = {"power": APF_OBJ_POWER, "splitter": APF_OBJ_SPLITTER}
 
-# Every symbol that include/apf.h declares.
+# Every symbol that include/*.h declares.
 EXPORTS = ("apf_create", "apf_destroy", "apf_set_grid", "apf_set_eps", "apf_set_channels",
            "apf_get_channels", "apf_solve_S", "apf_solve_S_grad", "apf_grad_from_gamma",
            "apf_set_refinement", "apf_get_stats", "apf_set_profiling", "apf_get_profile",
-           "apf_solve_S_noalloc", "apf_last_error", "apf_version")
+           "apf_solve_S_noalloc", "apf_last_error", "apf_version",
+           "apf_sno_create", "apf_sno_destroy", "apf_sno_num_params", "apf_sno_set_params",
+           "apf_sno_get_params", "apf_sno_forward", "apf_sno_gradients", "apf_sno_train_step")
 
 
 class APFError(RuntimeError):

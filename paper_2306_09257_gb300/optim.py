@@ -60,3 +60,60 @@ def optimize(solver, eps0: np.ndarray, eps_sub: float, eps_clad: float, j0: int,
     hist.evals = evals
     hist.seconds = time.perf_counter() - t0
     return eps, hist
+
+
+def optimize_screened(solver, sno, eps0: np.ndarray, eps_sub: float, eps_clad: float, j0: int,
+                      orders: Sequence[int], target: float, iters: int, gamma_max: float = None,
+                      n_candidates: int = 64, span: float = 2.0 ** -12, tau: float = 0.5, c1: float = 1e-2,
+                      eps_lo: float = 1.0, eps_hi: float = 2.25, max_backtracks: int = 12):
+    """Line search screened by the surrogate: every iteration scores
+    n_candidates step sizes (log-spaced from gamma_max down to
+    gamma_max * span) with the surrogate's efficiencies plugged into the
+    beam-splitter objective, and the exact solve judges the best one with the
+    same Armijo test as `optimize`; if it fails, backtracking by tau
+    continues from there.  The exact solve is therefore still the arbiter of
+    every accepted step."""
+    import torch
+
+    from . import surrogate as SG
+    eps = np.clip(np.asarray(eps0, np.float64).copy(), eps_lo, eps_hi)
+    t0 = time.perf_counter()
+    solver.set_eps(eps, eps_sub, eps_clad, j0=j0)
+    _, f, g = solver.solve_S_grad("splitter", orders, target)
+    mi, mo = solver.channels()
+    counts = torch.tensor([len(b) for b, _ in SG.pair_index(mi, mo, SG.ORDERS)], dtype=torch.float32,
+                          device=sno.device)
+    evals = 1
+    hist = History([f], 0, 0.0, [])
+    if gamma_max is None:
+        gamma_max = 0.25 / max(float(np.abs(g).max()), 1e-30)
+    gammas = gamma_max * span ** (np.arange(n_candidates) / max(1, n_candidates - 1))
+    screen_s = 0.0
+    for _ in range(iters):
+        ts = time.perf_counter()
+        e_t = torch.as_tensor(eps, dtype=torch.float32, device=sno.device)
+        g_t = torch.as_tensor(g, dtype=torch.float32, device=sno.device)
+        gam = torch.as_tensor(gammas, dtype=torch.float32, device=sno.device)[:, None, None]
+        cand = torch.clamp(e_t[None] - gam * g_t[None], eps_lo, eps_hi)
+        pred = SG.proxy_objective(sno.forward(cand), counts, target)
+        gamma = float(gammas[int(torch.argmin(pred))])
+        screen_s += time.perf_counter() - ts
+        accepted = False
+        for _ in range(max_backtracks):
+            trial = np.clip(eps - gamma * g, eps_lo, eps_hi)
+            solver.set_eps(trial, eps_sub, eps_clad, j0=j0)
+            _, ft, gt = solver.solve_S_grad("splitter", orders, target)
+            evals += 1
+            if ft <= f - c1 * float(np.sum((trial - eps) ** 2)) / gamma:
+                eps, f, g = trial, ft, gt
+                accepted = True
+                break
+            gamma *= tau
+        hist.gammas.append(gamma if accepted else 0.0)
+        hist.f.append(f)
+        if not accepted:
+            break
+    hist.evals = evals
+    hist.seconds = time.perf_counter() - t0
+    hist.screen_seconds = screen_s
+    return eps, hist

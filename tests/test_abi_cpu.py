@@ -18,7 +18,8 @@ def lib():
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "apf.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     return sorted(set(re.findall(r"\b(apf_[A-Za-z_]+)\s*\(", src)))
 
 
