@@ -231,3 +231,67 @@ def proxy_objective(Tbar: torch.Tensor, counts: torch.Tensor, target: float) -> 
     """Beam-splitter objective (Eq. 5) with every pair of order d replaced by
     the order's mean efficiency: sum_d n_d (T_d - t)^2."""
     return ((Tbar - target) ** 2 * counts).sum(-1)
+
+
+def main(argv=None):
+    """Surrogate study on the 1024 x 240 grid: exact training pairs from the
+    mixed solver, training in libapf, held-out error against the exact
+    efficiencies, and the screened line search against plain backtracking.
+    Prints one JSON line."""
+    import argparse
+    import json
+
+    from . import optim
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--designs", type=int, default=20000)
+    ap.add_argument("--holdout", type=int, default=512)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--threads", type=int, default=8)
+    ap.add_argument("--opt-iters", type=int, default=10)
+    ap.add_argument("--starts", type=int, default=3)
+    a = ap.parse_args(argv)
+    w = W.MID
+    X, T, t_gen = generate(w, range(1_000_000, 1_000_000 + a.designs), threads=a.threads)
+    n_tr = a.designs - a.holdout
+    sno = Surrogate(n=w.nx, in_ch=w.h, width=48, modes=64, layers=4, n_out=5, max_batch=256, seed=0)
+    tr = train(sno, X[:n_tr], T[:n_tr], epochs=a.epochs, batch=a.batch, lr=a.lr)
+    pred = sno.forward(X[n_tr:])
+    err = (pred - T[n_tr:])
+    mse = float((err ** 2).mean())
+    base = float(((T[:n_tr].mean(0, keepdim=True) - T[n_tr:]) ** 2).mean())
+    rel = float(torch.linalg.norm(err) / torch.linalg.norm(T[n_tr:]))
+    # inference rate on 64 candidates
+    cand = X[n_tr:n_tr + 64]
+    sno.forward(cand)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(20):
+        sno.forward(cand)
+    torch.cuda.synchronize()
+    t_inf = (time.perf_counter() - t0) / 20
+    runs = []
+    for k in range(a.starts):
+        eps0 = np.clip(w.eps_slab(2_000_000 + k), 1.0, 2.25)
+        s = _apf.solver_for_workload(w, eps0, precision="mixed")
+        _, hp = optim.optimize(s, eps0, w.eps_sub, w.eps_clad, w.j0, "splitter", list(ORDERS), 0.18,
+                               iters=a.opt_iters)
+        _, hs = optim.optimize_screened(s, sno, eps0, w.eps_sub, w.eps_clad, w.j0, list(ORDERS), 0.18,
+                                        iters=a.opt_iters)
+        s.close()
+        runs.append({"plain": {"f": hp.f, "exact_solves": hp.evals, "seconds": hp.seconds,
+                               "iters_per_s": hp.iters_per_second},
+                     "screened": {"f": hs.f, "exact_solves": hs.evals, "seconds": hs.seconds,
+                                  "iters_per_s": hs.iters_per_second, "screen_seconds": hs.screen_seconds}})
+    out = {"workload": w.name, "designs": a.designs, "holdout": a.holdout,
+           "data_seconds": t_gen, "data_rate_designs_per_s": a.designs / t_gen,
+           "train": {"steps": tr["steps"], "seconds": tr["seconds"], "final_loss": tr["losses"][-1]},
+           "heldout_mse": mse, "mean_predictor_mse": base, "heldout_rel_error": rel,
+           "inference_ms_64_candidates": 1e3 * t_inf, "optimisation": runs}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
