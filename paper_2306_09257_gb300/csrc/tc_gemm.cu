@@ -392,12 +392,17 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
         long long waves = (t + num_sms - 1) / num_sms;
         return (double)t / (double)(waves * num_sms);
     };
-    bool wide = (N > 128) && util(256) >= 0.9 * util(128);
+    // 128 x 256 tiles need ~25% less L2->SM operand traffic per flop; take them
+    // unless they waste much more of the last wave
+    bool wide = (N > 128) && util(256) >= 0.7 * util(128);
     int bn = wide ? 256 : 128;
     if (!make_map(&ma, A, BM) || !make_map(&mb, B, bn))
         return set_err(c, APF_ECUDA, "tensor map encode failed (M=%d N=%d kp=%lld)", M, N, A.kp);
     long long ntiles = (long long)((N + bn - 1) / bn) * ((M + BM - 1) / BM);
-    dim3 grid((unsigned)std::min<long long>(ntiles, num_sms));
+    // leave a few SMs free so that kernels of other streams (concurrent designs'
+    // diagonal-block inversions, which cannot share an SM with a GEMM CTA) progress
+    const int reserve = num_sms > 64 ? 4 : 0;
+    dim3 grid((unsigned)std::min<long long>(ntiles, num_sms - reserve));
     int pi = -1;
     if (c->prof_on && 2 * (c->prof_used + 1) <= (int)c->prof_ev.size()) {
         pi = c->prof_used++;
