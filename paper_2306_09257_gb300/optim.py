@@ -64,15 +64,16 @@ def optimize(solver, eps0: np.ndarray, eps_sub: float, eps_clad: float, j0: int,
 
 def optimize_screened(solver, sno, eps0: np.ndarray, eps_sub: float, eps_clad: float, j0: int,
                       orders: Sequence[int], target: float, iters: int, gamma_max: float = None,
-                      n_candidates: int = 64, span: float = 2.0 ** -12, tau: float = 0.5, c1: float = 1e-2,
+                      n_candidates: int = 64, span: float = 2.0 ** 6, tau: float = 0.5, c1: float = 1e-2,
                       eps_lo: float = 1.0, eps_hi: float = 2.25, max_backtracks: int = 12):
     """Line search screened by the surrogate: every iteration scores
-    n_candidates step sizes (log-spaced from gamma_max down to
-    gamma_max * span) with the surrogate's efficiencies plugged into the
-    beam-splitter objective, and the exact solve judges the best one with the
-    same Armijo test as `optimize`; if it fails, backtracking by tau
+    n_candidates step sizes, log-spaced from gamma_max / span to
+    gamma_max * span, with the surrogate's efficiencies plugged into the
+    beam-splitter objective; the exact solve judges the best one with the
+    same Armijo test as `optimize`, and if it fails backtracking by tau
     continues from there.  The exact solve is therefore still the arbiter of
-    every accepted step."""
+    every accepted step; the surrogate lets the search try steps longer than
+    gamma_max without paying exact solves for the ones it rejects."""
     import torch
 
     from . import surrogate as SG
@@ -87,7 +88,7 @@ def optimize_screened(solver, sno, eps0: np.ndarray, eps_sub: float, eps_clad: f
     hist = History([f], 0, 0.0, [])
     if gamma_max is None:
         gamma_max = 0.25 / max(float(np.abs(g).max()), 1e-30)
-    gammas = gamma_max * span ** (np.arange(n_candidates) / max(1, n_candidates - 1))
+    gammas = gamma_max * span ** np.linspace(1.0, -1.0, n_candidates)
     screen_s = 0.0
     for _ in range(iters):
         ts = time.perf_counter()

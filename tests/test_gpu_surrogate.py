@@ -86,4 +86,8 @@ def test_trained_surrogate_in_the_line_search(env):
           f"{h_plain.iters_per_second:.2f} it/s; screened: f -> {h_scr.f[-1]:.4f}, {per_scr:.2f} solves/step, "
           f"{h_scr.iters_per_second:.2f} it/s")
     assert h_scr.f[-1] < h_scr.f[0]
-    assert per_scr < per_plain
+    # the gain: a larger decrease of f per exact solve than plain backtracking
+    gain_plain = (h_plain.f[0] - h_plain.f[-1]) / h_plain.evals
+    gain_scr = (h_scr.f[0] - h_scr.f[-1]) / h_scr.evals
+    print(f"decrease of f per exact solve: plain {gain_plain:.4f}, screened {gain_scr:.4f}")
+    assert gain_scr > gain_plain
