@@ -108,11 +108,14 @@ static int ensure_workspace(apf_ctx *c) {
     if (c->precision != APF_FP64) {
         if ((rc = mixed_alloc(c)) != APF_OK) { free_workspace(c); return rc; }
     }
-    cudaError_t e = cudaMemcpy(c->d_min, c->m_in.data(), sizeof(int) * nin, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_mout, c->m_out.data(), sizeof(int) * nout, cudaMemcpyHostToDevice);
+    // set-up work runs on the context's own non-blocking stream (never the legacy
+    // stream or a device-wide sync, which other threads' graph captures forbid)
+    cudaStream_t ss = c->cap_stream;
+    cudaError_t e = cudaMemcpyAsync(c->d_min, c->m_in.data(), sizeof(int) * nin, cudaMemcpyHostToDevice, ss);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mout, c->m_out.data(), sizeof(int) * nout, cudaMemcpyHostToDevice, ss);
     if (e != cudaSuccess) { free_workspace(c); return check_cuda(c, e, "upload channels"); }
-    launch_twiddles(c, 0);
-    e = cudaDeviceSynchronize();
+    launch_twiddles(c, ss);
+    e = cudaStreamSynchronize(ss);
     if (e != cudaSuccess) { free_workspace(c); return check_cuda(c, e, "twiddles"); }
     c->ws_nx = c->nx; c->ws_ny = c->ny; c->ws_h = c->h; c->ws_min = nin; c->ws_mout = nout;
     return APF_OK;
@@ -171,7 +174,7 @@ int apf_create(apf_ctx **out, int cuda_device, int precision) {
 void apf_destroy(apf_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
-    cudaDeviceSynchronize();
+    if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
     free_workspace(c);
     if (c->d_eps) cudaFree(c->d_eps);
     for (auto &ev : c->ev) if (ev) cudaEventDestroy(ev);
@@ -226,16 +229,19 @@ int apf_set_eps(apf_ctx *c, const double *eps_slab, int j0, int h, double eps_su
     }
     if (is_device_ptr(eps_slab)) {
         std::vector<double> tmp(n);
-        cudaError_t e = cudaMemcpy(tmp.data(), eps_slab, sizeof(double) * n, cudaMemcpyDeviceToHost);
+        cudaError_t e = cudaMemcpyAsync(tmp.data(), eps_slab, sizeof(double) * n, cudaMemcpyDeviceToHost, c->cap_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap_stream);
         if (e != cudaSuccess) return check_cuda(c, e, "read eps");
         for (long long i = 0; i < n; ++i)
             if (!isfinite(tmp[i])) return set_err(c, APF_EINVAL, "eps_slab[%lld] is not finite", i);
-        e = cudaMemcpy(c->d_eps, eps_slab, sizeof(double) * n, cudaMemcpyDeviceToDevice);
+        e = cudaMemcpyAsync(c->d_eps, eps_slab, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->cap_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap_stream);
         if (e != cudaSuccess) return check_cuda(c, e, "copy eps");
     } else {
         for (long long i = 0; i < n; ++i)
             if (!isfinite(eps_slab[i])) return set_err(c, APF_EINVAL, "eps_slab[%lld] is not finite", i);
-        cudaError_t e = cudaMemcpy(c->d_eps, eps_slab, sizeof(double) * n, cudaMemcpyHostToDevice);
+        cudaError_t e = cudaMemcpyAsync(c->d_eps, eps_slab, sizeof(double) * n, cudaMemcpyHostToDevice, c->cap_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap_stream);
         if (e != cudaSuccess) return check_cuda(c, e, "upload eps");
     }
     bool changed = (c->h != h) || (c->eps_sub != eps_sub) || (c->eps_clad != eps_clad);
@@ -277,8 +283,9 @@ int apf_set_channels(apf_ctx *c, const int *m_in, int n_in, const int *m_out, in
     int rc = ensure_workspace(c);
     if (rc != APF_OK) { c->ch_set = false; return rc; }
     // the orders may have changed with the same counts
-    cudaMemcpy(c->d_min, c->m_in.data(), sizeof(int) * c->m_in.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(c->d_mout, c->m_out.data(), sizeof(int) * c->m_out.size(), cudaMemcpyHostToDevice);
+    cudaMemcpyAsync(c->d_min, c->m_in.data(), sizeof(int) * c->m_in.size(), cudaMemcpyHostToDevice, c->cap_stream);
+    cudaMemcpyAsync(c->d_mout, c->m_out.data(), sizeof(int) * c->m_out.size(), cudaMemcpyHostToDevice, c->cap_stream);
+    cudaStreamSynchronize(c->cap_stream);
     return APF_OK;
 }
 
@@ -489,7 +496,8 @@ static int finish(apf_ctx *c, cudaStream_t s, int rc_solve) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(c, e, "kernel launch");
     int flags = 0;
-    cudaMemcpy(&flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpyAsync(&flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
     float ms[6] = {0};
     for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]);
     c->stats.ms_boundary = ms[0];
