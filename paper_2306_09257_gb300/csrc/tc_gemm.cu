@@ -310,6 +310,180 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+__device__ __forceinline__ void tma_load_3d_mc(void *smem_dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                               int c2, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
+        "[%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(smem_dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Two-CTA cluster variant: the CTAs of a cluster compute vertically adjacent
+// 128-row tiles that share one B tile; each CTA loads half of that B tile
+// with a cluster multicast into both CTAs' shared memory, and each MMA
+// completion is committed to the stage barriers of both CTAs (a stage is
+// refilled only when both have consumed it).  Halves the B traffic per SM.
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm_mc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+    using L = Layout<BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + L::BAR);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rank = (int)cluster_rank();
+    const int Mt = (p.M + BM - 1) / BM, Mp = (Mt + 1) / 2, Nt = (p.N + BN - 1) / BN;
+    const int npairs = Mp * Nt;
+    const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+    const int total = p.nseg * p.kblocks;
+    constexpr int HALF = BN / 2;
+    constexpr int HALF_BYTES = HALF * BK * 2;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 2);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2 * BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    cluster_sync();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+    int issued = 0;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            for (int pt = cid; pt < npairs && ok; pt += ncl) {
+                const int m0 = (2 * (pt % Mp) + rank) * BM, n0 = (pt / Mp) * BN;
+                for (int kk = 0; kk < total; ++kk, ++it) {
+                    const int s = it % STAGES, r = it / STAGES;
+                    if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    const int seg = kk / p.kblocks, kb = kk - seg * p.kblocks;
+                    const int pa = (p.seg_pairs >> (4 * seg + 2)) & 3, pb = (p.seg_pairs >> (4 * seg)) & 3;
+                    uint8_t *sa = smem + s * L::STAGE;
+                    uint8_t *sb = sa + L::A_BYTES;
+                    mbar_expect_tx(&full[s], L::A_BYTES + L::B_BYTES);
+                    tma_load_3d(sa, &tmA, &full[s], kb * BK, m0, pa);
+                    tma_load_3d_mc(sb + rank * HALF_BYTES, &tmB, &full[s], kb * BK, n0 + rank * HALF, pb,
+                                   (uint16_t)3);
+                    issued = it + 1;
+                }
+            }
+            // wait until both CTAs have released the last round of every stage, so
+            // that no commit from the peer is still on its way to this CTA
+            if (ok) {
+                for (int it2 = issued > STAGES ? issued - STAGES : 0; it2 < issued; ++it2)
+                    if (!mbar_wait(&empty[it2 % STAGES], (it2 / STAGES) & 1, abort_flag)) { ok = false; break; }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                   ((uint32_t)(BM >> 4) << 24);
+            int it = 0, tl = 0;
+            for (int pt = cid; pt < npairs && ok; pt += ncl, ++tl) {
+                const int b = tl & 1, u = tl >> 1;
+                if (!mbar_wait(&tempty[b], (u & 1) ^ 1, abort_flag)) { ok = false; break; }
+                fence_after();
+                const uint32_t acc = tmem + (uint32_t)(b * BN);
+                for (int kk = 0; kk < total; ++kk, ++it) {
+                    const int s = it % STAGES, r = it / STAGES;
+                    if (!mbar_wait(&full[s], r & 1, abort_flag)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t sa = smem_u32(smem + s * L::STAGE);
+                    const uint32_t sb = sa + L::A_BYTES;
+#pragma unroll
+                    for (int k4 = 0; k4 < BK / 16; ++k4)
+                        mma_bf16(acc, sw128_desc(sa + k4 * 32), sw128_desc(sb + k4 * 32), idesc,
+                                 (kk > 0 || k4 > 0) ? 1u : 0u);
+                    mma_commit_mc(&empty[s], (uint16_t)3);
+                }
+                if (!ok) break;
+                mma_commit(&tfull[b]);
+            }
+            if (!ok) {
+                mma_commit(&tfull[0]);
+                mbar_wait(&tfull[0], 0, abort_flag, true);
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        int tl = 0;
+        for (int pt = cid; pt < npairs; pt += ncl, ++tl) {
+            const int b = tl & 1, u = tl >> 1;
+            if (!mbar_wait(&tfull[b], u & 1, abort_flag)) { ok = false; break; }
+            fence_after();
+            const int m0 = (2 * (pt % Mp) + rank) * BM, n0 = (pt / Mp) * BN;
+            const int row = m0 + 32 * q + lane;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + c), r);
+                store_chunk(p, row, n0 + c, r);
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+    }
+    if (!ok) {
+        *abort_flag = 1;
+        if (p.flags) atomicOr(p.flags, FLAG_TIMEOUT);
+    }
+    __syncwarp();
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        for (int it = issued > STAGES ? issued - STAGES : 0; it < issued; ++it)
+            mbar_wait(&full[it % STAGES], (it / STAGES) & 1, abort_flag, true);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+    }
+    cluster_sync();
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool ensure_encode() {
@@ -360,7 +534,12 @@ uint32_t tc_seg_pairs(int nsplit, int *nseg) {
 void tc_init_attrs() {
     set_attr<256, 4>();
     set_attr<128, 6>();
+    cudaFuncSetAttribute(k_tc_gemm_mc<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<256, 4>::TOTAL);
+    cudaFuncSetAttribute(k_tc_gemm_mc<256, 4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
 }
+
+// 0: one CTA per tile; 1: two-CTA clusters sharing B tiles (wide tiles only).
+int g_tc_cluster_mode = 1;
 
 int tc_init() { return ensure_encode() ? APF_OK : APF_ECUDA; }
 
@@ -413,8 +592,32 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
         record_event(c, c->prof_ev[2 * pi], s);
     }
     constexpr int smem_wide = Layout<256, 4>::TOTAL, smem_narrow = Layout<128, 6>::TOTAL;
-    if (wide) APF_LAUNCH(c, (k_tc_gemm<256, 4>), grid, 192, smem_wide, s, ma, mb, p);
-    else APF_LAUNCH(c, (k_tc_gemm<128, 6>), grid, 192, smem_narrow, s, ma, mb, p);
+    const int mt = (M + BM - 1) / BM;
+    if (wide && g_tc_cluster_mode == 1 && mt >= 2) {
+        CUtensorMap mbh;
+        if (!make_map(&mbh, B, 128)) return set_err(c, APF_ECUDA, "tensor map encode failed (half B)");
+        long long npairs = (long long)((mt + 1) / 2) * ((N + 255) / 256);
+        long long ncl = std::min<long long>(npairs, (num_sms - reserve) / 2);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(2 * ncl));
+        cfg.blockDim = dim3(192);
+        cfg.dynamicSmemBytes = smem_wide;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_gemm_mc<256, 4>, ma, mbh, p);
+        if (e != cudaSuccess) return check_cuda(c, e, "cluster GEMM launch");
+        c->launches++;
+    } else if (wide) {
+        APF_LAUNCH(c, (k_tc_gemm<256, 4>), grid, 192, smem_wide, s, ma, mb, p);
+    } else {
+        APF_LAUNCH(c, (k_tc_gemm<128, 6>), grid, 192, smem_narrow, s, ma, mb, p);
+    }
     if (pi >= 0) record_event(c, c->prof_ev[2 * pi + 1], s);
     return APF_OK;
 }
