@@ -49,6 +49,8 @@ def args_parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--solves", type=int, default=4, help="oracle solves per CPU sample")
+    p.add_argument("--refine-tol", type=float, default=None,
+                   help="refinement tolerance of the mixed solves (library default if omitted)")
     p.add_argument("--concurrent", type=int, default=4,
                    help="independent designs in flight per GPU (one context + stream + host thread each)")
     return p.parse_args()
@@ -212,6 +214,9 @@ def main():
     eps_host = [[w.eps_slab(sd) for sd in row] for row in replicas.replica_seeds(rank, B, nseeds)]
     eps_dev = [[torch.tensor(e, device=dev) for e in row] for row in eps_host]
     solvers = [apf.solver_for_workload(w, eps_host[b][0], precision="mixed", device=local) for b in range(B)]
+    if a.refine_tol is not None:
+        for sv in solvers:
+            sv.set_refinement(a.refine_tol, 8)
     s = solvers[0]
     m_in, m_out = s.channels()
     streams = [torch.cuda.Stream(device=dev) for _ in range(B)]
@@ -344,7 +349,7 @@ def main():
                            "parallelism": f"replicas x{ws}, {B} independent designs per GPU"},
                 "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu,
-                "fp64": fp64, "concurrent_designs": B,
+                "fp64": fp64, "concurrent_designs": B, "refine_tol": a.refine_tol if a.refine_tol else 1e-10,
                 "stages_ms": {k: st_last[k] for k in ("ms_boundary", "ms_eliminate", "ms_fields", "ms_readout",
                                                        "ms_gradient")},
                 "gemm": {"launches": prof["gemm_launches"], "ms": prof["gemm_ms"]}}
