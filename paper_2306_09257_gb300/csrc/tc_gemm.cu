@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <stdlib.h>
 
 namespace {
 
@@ -580,7 +581,13 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
     long long ntiles = (long long)((N + bn - 1) / bn) * ((M + BM - 1) / BM);
     // leave a few SMs free so that kernels of other streams (concurrent designs'
     // diagonal-block inversions, which cannot share an SM with a GEMM CTA) progress
-    const int reserve = num_sms > 64 ? 4 : 0;
+    static int reserve = -1;
+    if (reserve < 0) {
+        const char *e = getenv("APF_GEMM_RESERVED_SMS");  // tuning knob; default 4
+        reserve = e ? atoi(e) : 4;
+        if (reserve < 0 || reserve > num_sms / 2) reserve = 4;
+        if (num_sms <= 64) reserve = 0;
+    }
     dim3 grid((unsigned)std::min<long long>(ntiles, num_sms - reserve));
     int pi = -1;
     if (c->prof_on && 2 * (c->prof_used + 1) <= (int)c->prof_ev.size()) {
