@@ -155,7 +155,7 @@ constexpr int leaf_smem_bytes(int elem_bytes) {
 template <int NB>
 __device__ void leaf_gj_regs(float *re, float *im, long long ld, int *flags) {
     constexpr int Q = NB / 4;
-    __shared__ float2 prowa[NB], prowb[NB];  // (re, im) and (im, re) of the published pivot row
+    __shared__ float2 prow[NB];
     __shared__ float mag[NB];
     __shared__ int piv[NB], ipiv[NB];
     __shared__ int s_p;
@@ -209,19 +209,21 @@ __device__ void leaf_gj_regs(float *re, float *im, long long ld, int *flags) {
                 float2 x = (j == k) ? pinv
                                     : make_float2(a[q].x * pinv.x - a[q].y * pinv.y, a[q].x * pinv.y + a[q].y * pinv.x);
                 a[q] = x;
-                const float2 pv = (j == k) ? make_float2(1.f + pinv.x, pinv.y) : x;
-                prowa[j] = pv;
-                prowb[j] = make_float2(pv.y, pv.x);
+                prow[j] = (j == k) ? make_float2(1.f + pinv.x, pinv.y) : x;
             }
         }
         __syncthreads();
         if (i != p) {
-            // x -= f * pr as two packed fp32x2 FMAs: (-f.x, -f.x) * (pr.x, pr.y) and (f.y, -f.y) * (pr.y, pr.x)
-            const float2 m1 = make_float2(-f.x, -f.x), m2 = make_float2(f.y, -f.y);
+            const float nfx = -f.x, fy = f.y;
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                float2 x = __ffma2_rn(m1, prowa[sub + 4 * q], a[q]);
-                a[q] = __ffma2_rn(m2, prowb[sub + 4 * q], x);
+                const float2 pr = prow[sub + 4 * q];
+                float2 x = a[q];
+                x.x = fmaf(nfx, pr.x, x.x);
+                x.x = fmaf(fy, pr.y, x.x);
+                x.y = fmaf(nfx, pr.y, x.y);
+                x.y = fmaf(-fy, pr.x, x.y);
+                a[q] = x;
             }
         }
         // next pivot column: a uniform switch on its register slot
