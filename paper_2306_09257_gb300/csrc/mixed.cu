@@ -19,10 +19,10 @@
 struct MixedWork {
     int nsplit_elim = 2, nsplit_grad = 3, leaf = 128, leaf_variant = 0;
     float *Xre = nullptr, *Xim = nullptr;            // n x n working block
+    float *Tre = nullptr, *Tim = nullptr;            // recursion scratch (n*n/2 each)
+    float *Vre = nullptr, *Vim = nullptr;
     __nv_bfloat16 *PA = nullptr, *PB = nullptr;      // operand packs
     long long pa_elems = 0, pb_elems = 0;
-    __nv_bfloat16 *LV = nullptr;                     // per-recursion-level packs of T and V
-    std::vector<long long> lv_off;                   // element offset of each level
     __nv_bfloat16 *GP = nullptr;                     // packed G_j, h of them
     long long gp_stride = 0;
     float *O32 = nullptr;                            // GEMM output planes, 2 * max(ncol, n_out) * nx
@@ -300,6 +300,31 @@ __global__ void __launch_bounds__(NB * 4) k_leaf32r2(float *re, float *im, long 
     leaf_gj_regs2<NB>(re, im, ld, flags);
 }
 
+// C block <- -V, B block <- -V^T (planar float32).
+__global__ void k_negoff32(float *Bre, float *Bim, float *Cre, float *Cim, long long ld, const float *Vre,
+                           const float *Vim, int h) {
+    __shared__ float tr[32][33], ti[32][33];
+    int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    int tx = threadIdx.x, ty = threadIdx.y;
+    for (int i = ty; i < 32; i += 8) {
+        int gi = i0 + i, gj = j0 + tx;
+        if (gi < h && gj < h) {
+            float vr = Vre[(long long)gi * h + gj], vi = Vim[(long long)gi * h + gj];
+            Cre[(long long)gi * ld + gj] = -vr;
+            Cim[(long long)gi * ld + gj] = -vi;
+            tr[i][tx] = vr; ti[i][tx] = vi;
+        }
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        int gj = j0 + i, gi = i0 + tx;  // B[gj][gi] = -V[gi][gj]
+        if (gi < h && gj < h) {
+            Bre[(long long)gj * ld + gi] = -tr[tx][i];
+            Bim[(long long)gj * ld + gi] = -ti[tx][i];
+        }
+    }
+}
+
 // E[c][x] = (R ? R[c][x] : 0) + O[c][x] for c < mcols;  E = R for c >= mcols.
 __global__ void k_combine(double2 *E, const double2 *R, const float *Ore, const float *Oim, int ncol, int mcols,
                           int nx) {
@@ -496,10 +521,8 @@ PackView pack64BT(apf_ctx *c, __nv_bfloat16 *dst, const double2 *src, long long 
 int leaf_size(const MixedWork *w) { return w->leaf; }
 
 // X <- X^-1 in place for complex-symmetric X, the 2x2 block Schur recursion of
-// the float64 path with all four products on the tensor cores:
-//   T = C Ai (emitted only as its packs), D <- D - T B, D <- D^-1 (= Si),
-//   C <- -Si T, B <- (-Si T)^T (one product, three outputs), A <- A + (Si T)^T T.
-int inv32(apf_ctx *c, const PV &X, int n, int depth, cudaStream_t s) {
+// the float64 path with all four products on the tensor cores.
+int inv32(apf_ctx *c, const PV &X, int n, float *Tre, float *Tim, float *Vre, float *Vim, cudaStream_t s) {
     MixedWork *w = c->mw;
     if (n <= leaf_size(w)) {
         if (n == 128 && w->leaf_variant == 1)
@@ -520,47 +543,29 @@ int inv32(apf_ctx *c, const PV &X, int n, int depth, cudaStream_t s) {
             APF_LAUNCH(c, k_leaf_inv32, 1, 256, n * n * (int)sizeof(float2), s, X.re, X.im, X.ld, n, c->d_flags);
         return APF_OK;
     }
-    if (depth >= (int)w->lv_off.size()) return set_err(c, APF_EINVAL, "recursion deeper than the level buffers");
-    const int h = n / 2;
-    const int ns = w->nsplit_elim;
-    const long long hh = h;
+    int h = n / 2;
+    int ns = w->nsplit_elim;
     PV A = X, B = X.off(0, h), C = X.off(h, 0), D = X.off(h, h);
-    __nv_bfloat16 *lv = w->LV + w->lv_off[depth];
-    __nv_bfloat16 *TA = lv;                        // T as A operand: h x 2h
-    __nv_bfloat16 *TB = TA + 2 * hh * hh * ns;     // T^T as B operand: 2h x 2h
-    __nv_bfloat16 *VA = TB + 4 * hh * hh * ns;     // (-V)^T as A operand: h x 2h
-    const PackView tA{TA, hh, 2 * hh, ns, 2 * hh * hh}, tB{TB, 2 * hh, 2 * hh, ns, 4 * hh * hh},
-        vA{VA, hh, 2 * hh, ns, 2 * hh * hh};
+    PV T{Tre, Tim, h}, V{Vre, Vim, h};
+    long long hh = (long long)h * h;
     int rc;
-    if ((rc = inv32(c, A, h, depth + 1, s))) return rc;
+    if ((rc = inv32(c, A, h, Tre + hh, Tim + hh, Vre + hh, Vim + hh, s))) return rc;
     // T = C Ai
     PackView pa, pb;
     pack2(c, &pa, w->PA, C, h, h, false, &pb, w->PB, A, h, h, false, ns, s);
-    {
-        TcSinks sk;
-        sk.skip_fp32 = true;
-        sk.nsplit = ns;
-        sk.pkA = TA; sk.pkA_kp = 2 * hh; sk.pkA_pitch = 2 * hh * hh;
-        sk.pkBT = TB; sk.pkBT_kp = 2 * hh; sk.pkBT_pitch = 4 * hh * hh;
-        if ((rc = tc_gemm_ex(c, pa, pb, ns, h, 2 * h, h, 1.f, 0.f, nullptr, nullptr, 0, nullptr, nullptr, 0, sk, s)))
-            return rc;
-    }
+    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, 1.f, 0.f, T.re, T.im, T.ld, nullptr, nullptr, 0, s))) return rc;
     // D = D - T B   (B-operand columns = rows of C)
-    pb = pack32(c, w->PB, C, h, h, false, true, ns, s);
-    if ((rc = tc_gemm(c, tA, pb, ns, h, 2 * h, h, -1.f, 1.f, D.re, D.im, D.ld, D.re, D.im, D.ld, s))) return rc;
-    if ((rc = inv32(c, D, h, depth + 1, s))) return rc;
-    // -V = -Si T  ->  C block, its transpose -> B block, and (-V)^T packed as an A operand
-    pa = pack32(c, w->PA, D, h, h, false, false, ns, s);
-    {
-        TcSinks sk;
-        sk.nsplit = ns;
-        sk.t_re = B.re; sk.t_im = B.im; sk.ldt = X.ld;
-        sk.pkAT = VA; sk.pkAT_kp = 2 * hh; sk.pkAT_pitch = 2 * hh * hh;
-        if ((rc = tc_gemm_ex(c, pa, tB, ns, h, 2 * h, h, -1.f, 0.f, C.re, C.im, C.ld, nullptr, nullptr, 0, sk, s)))
-            return rc;
-    }
-    // A = Ai + V^T T = Ai - (-V)^T T
-    if ((rc = tc_gemm(c, vA, tB, ns, h, 2 * h, h, -1.f, 1.f, A.re, A.im, A.ld, A.re, A.im, A.ld, s))) return rc;
+    pack2(c, &pa, w->PA, T, h, h, false, &pb, w->PB, C, h, h, false, ns, s);
+    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, -1.f, 1.f, D.re, D.im, D.ld, D.re, D.im, D.ld, s))) return rc;
+    if ((rc = inv32(c, D, h, Tre + hh, Tim + hh, Vre + hh, Vim + hh, s))) return rc;
+    // V = Si T
+    pack2(c, &pa, w->PA, D, h, h, false, &pb, w->PB, T, h, h, true, ns, s);
+    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, 1.f, 0.f, V.re, V.im, V.ld, nullptr, nullptr, 0, s))) return rc;
+    // A = Ai + V^T T
+    pa = pack32(c, w->PA, V, h, h, true, false, ns, s);
+    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, 1.f, 1.f, A.re, A.im, A.ld, A.re, A.im, A.ld, s))) return rc;
+    dim3 grid((h + 31) / 32, (h + 31) / 32);
+    APF_LAUNCH(c, k_negoff32, grid, dim3(32, 8), 0, s, B.re, B.im, C.re, C.im, X.ld, V.re, V.im, h);
     return APF_OK;
 }
 
@@ -640,6 +645,7 @@ int mixed_alloc(apf_ctx *c) {
     int rc;
 #define WA(p, cnt) if ((rc = walloc(c, w, &(p), (cnt))) != APF_OK) return rc;
     WA(w->Xre, n * n); WA(w->Xim, n * n);
+    WA(w->Tre, n * n / 2); WA(w->Tim, n * n / 2); WA(w->Vre, n * n / 2); WA(w->Vim, n * n / 2);
     int ns_max = std::max(w->nsplit_elim, w->nsplit_grad);
     // A operands: recursion (h x 2h), fields (ncol x 2n), Gamma (n_out x kp)
     long long kp_g = round_up(2LL * nin, 64);
@@ -648,15 +654,6 @@ int mixed_alloc(apf_ctx *c) {
     w->pb_elems = std::max(n * n * w->nsplit_elim, 2 * n * kp_g * ns_max);
     WA(w->PA, w->pa_elems);
     WA(w->PB, w->pb_elems);
-    {
-        // level d (child size hh = n >> (d+1)): T as A (hh x 2hh), T^T as B (2hh x 2hh), (-V)^T as A (hh x 2hh)
-        long long tot = 0;
-        for (long long hh = n / 2; hh >= 1 && hh * 2 > std::min(w->leaf, 64); hh /= 2) {
-            w->lv_off.push_back(tot);
-            tot += 8 * hh * hh * w->nsplit_elim;
-        }
-        WA(w->LV, std::max<long long>(tot, 1));
-    }
     w->gp_stride = 2 * n * 2 * n * w->nsplit_elim;
     WA(w->GP, h * w->gp_stride);
     WA(w->O32, 2 * std::max<long long>(ncol, nout) * n);
@@ -677,7 +674,7 @@ int mixed_eliminate(apf_ctx *c, cudaStream_t s) {
     APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, 0, c->d_eps, c->d_circ, (const float *)nullptr,
                (const float *)nullptr, w->Xre, w->Xim);
     for (int j = 0; j < c->h; ++j) {
-        int rc = inv32(c, X, n, 0, s);
+        int rc = inv32(c, X, n, w->Tre, w->Tim, w->Vre, w->Vim, s);
         if (rc) return rc;
         pack32(c, w->GP + j * w->gp_stride, X, n, n, false, true, w->nsplit_elim, s);
         if (j + 1 < c->h)
@@ -806,7 +803,7 @@ extern "C" int apf_debug_inv32(apf_ctx *c, int n, float *re, float *im, int leaf
     // leaf = block size + 1000 * kernel variant (test and tuning hook)
     if (leaf > 0) { c->mw->leaf = leaf % 1000; c->mw->leaf_variant = leaf / 1000; }
     cudaMemset(c->d_flags, 0, 16);
-    int rc = inv32(c, PV{re, im, n}, n, 0, 0);
+    int rc = inv32(c, PV{re, im, n}, n, c->mw->Tre, c->mw->Tim, c->mw->Vre, c->mw->Vim, 0);
     cudaError_t e = cudaDeviceSynchronize();
     c->mw->leaf = old;
     c->mw->leaf_variant = oldv;

@@ -133,74 +133,33 @@ struct Layout {
     static constexpr int TOTAL = BAR + (2 * STAGES + 4) * 8 + 16 + 1024;
 };
 
-__device__ __forceinline__ void bsplit(float x, int ns, __nv_bfloat16 *o) {
-    __nv_bfloat16 h0 = __float2bfloat16_rn(x);
-    o[0] = h0;
-    if (ns > 1) {
-        float x1 = x - __bfloat162float(h0);
-        __nv_bfloat16 h1 = __float2bfloat16_rn(x1);
-        o[1] = h1;
-        if (ns > 2) o[2] = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-    }
-}
-
-// Extra outputs of one value at output (row, col).
-__device__ __forceinline__ void sinks(const TcParams &p, int row, int col, float v) {
-    const bool re = col < p.n_cplx;
-    const int c = re ? col : col - p.n_cplx;
-    if (p.t_re) (re ? p.t_re : p.t_im)[(long long)c * p.ldt + row] = v;
-    if (p.pkA || p.pkBT || p.pkAT) {
-        __nv_bfloat16 sp[3], sn[3];
-        bsplit(v, p.pk_nsplit, sp);
-        for (int q = 0; q < p.pk_nsplit; ++q) sn[q] = __hneg(sp[q]);
-        for (int q = 0; q < p.pk_nsplit; ++q) {
-            if (p.pkA) p.pkA[q * p.pkA_pitch + (long long)row * p.pkA_kp + col] = sp[q];
-            if (p.pkBT) {
-                __nv_bfloat16 *o = p.pkBT + q * p.pkBT_pitch;
-                if (re) {
-                    o[(long long)c * p.pkBT_kp + row] = sp[q];
-                    o[(long long)(p.n_cplx + c) * p.pkBT_kp + p.kM + row] = sp[q];
-                } else {
-                    o[(long long)c * p.pkBT_kp + p.kM + row] = sn[q];
-                    o[(long long)(p.n_cplx + c) * p.pkBT_kp + row] = sp[q];
-                }
-            }
-            if (p.pkAT)
-                p.pkAT[q * p.pkAT_pitch + (long long)c * p.pkAT_kp + (re ? 0 : p.kM) + row] = sp[q];
-        }
-    }
-}
-
 // Epilogue of one 32-column chunk of one accumulator row.
 __device__ __forceinline__ void store_chunk(const TcParams &p, int row, int col0, const uint32_t (&r)[32]) {
     if (row >= p.M) return;
     const bool use_beta = (p.beta != 0.0f);
-    const bool extra = p.t_re || p.pkA || p.pkBT || p.pkAT;
     float *op;
     const float *ip;
     int cc0;
     if (col0 < p.n_cplx) { op = p.out_re; ip = p.in_re; cc0 = col0; }
     else { op = p.out_im; ip = p.in_im; cc0 = col0 - p.n_cplx; }
     const bool whole = (col0 + 32 <= p.N) && ((col0 < p.n_cplx) == (col0 + 31 < p.n_cplx));
-    if (op && !extra && whole) {
-        float *dst = op + (long long)row * p.ldo + cc0;
-        const float *src = ip + (long long)row * p.ldi + cc0;
-        if (((((uintptr_t)dst) | (use_beta ? (uintptr_t)src : 0)) & 15) == 0) {
+    float *dst = op + (long long)row * p.ldo + cc0;
+    const float *src = ip + (long long)row * p.ldi + cc0;
+    if (whole && ((((uintptr_t)dst) | (use_beta ? (uintptr_t)src : 0)) & 15) == 0) {
 #pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                float4 o;
-                o.x = p.alpha * __uint_as_float(r[4 * v + 0]);
-                o.y = p.alpha * __uint_as_float(r[4 * v + 1]);
-                o.z = p.alpha * __uint_as_float(r[4 * v + 2]);
-                o.w = p.alpha * __uint_as_float(r[4 * v + 3]);
-                if (use_beta) {
-                    float4 cv = *reinterpret_cast<const float4 *>(src + 4 * v);
-                    o.x += p.beta * cv.x; o.y += p.beta * cv.y; o.z += p.beta * cv.z; o.w += p.beta * cv.w;
-                }
-                *reinterpret_cast<float4 *>(dst + 4 * v) = o;
+        for (int v = 0; v < 8; ++v) {
+            float4 o;
+            o.x = p.alpha * __uint_as_float(r[4 * v + 0]);
+            o.y = p.alpha * __uint_as_float(r[4 * v + 1]);
+            o.z = p.alpha * __uint_as_float(r[4 * v + 2]);
+            o.w = p.alpha * __uint_as_float(r[4 * v + 3]);
+            if (use_beta) {
+                float4 c = *reinterpret_cast<const float4 *>(src + 4 * v);
+                o.x += p.beta * c.x; o.y += p.beta * c.y; o.z += p.beta * c.z; o.w += p.beta * c.w;
             }
-            return;
+            *reinterpret_cast<float4 *>(dst + 4 * v) = o;
         }
+        return;
     }
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
@@ -213,8 +172,7 @@ __device__ __forceinline__ void store_chunk(const TcParams &p, int row, int col0
         else { o2 = p.out_im; i2 = p.in_im; cc = col - p.n_cplx; }
         float v = p.alpha * __uint_as_float(r[i]);
         if (use_beta) v += p.beta * i2[(long long)row * p.ldi + cc];
-        if (o2) o2[(long long)row * p.ldo + cc] = v;
-        if (extra) sinks(p, row, col, v);
+        o2[(long long)row * p.ldo + cc] = v;
     }
 }
 
@@ -589,12 +547,6 @@ int tc_init() { return ensure_encode() ? APF_OK : APF_ECUDA; }
 int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M, int N, int n_cplx, float alpha,
             float beta, float *out_re, float *out_im, long long ldo, const float *in_re, const float *in_im,
             long long ldi, cudaStream_t s) {
-    return tc_gemm_ex(c, A, B, nsplit, M, N, n_cplx, alpha, beta, out_re, out_im, ldo, in_re, in_im, ldi, TcSinks{}, s);
-}
-
-int tc_gemm_ex(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M, int N, int n_cplx, float alpha,
-               float beta, float *out_re, float *out_im, long long ldo, const float *in_re, const float *in_im,
-               long long ldi, const TcSinks &sk, cudaStream_t s) {
     if (M <= 0 || N <= 0) return APF_OK;
     if (!ensure_encode()) return set_err(c, APF_ECUDA, "cuTensorMapEncodeTiled unavailable");
     if (A.kp != B.kp || A.kp % BK != 0) return set_err(c, APF_EINVAL, "tc_gemm: K mismatch (%lld vs %lld)", A.kp, B.kp);
@@ -606,14 +558,6 @@ int tc_gemm_ex(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int
     p.out_re = out_re; p.out_im = out_im; p.ldo = ldo;
     p.in_re = in_re ? in_re : out_re; p.in_im = in_im ? in_im : out_im; p.ldi = in_re ? ldi : ldo;
     p.flags = c->d_flags;
-    if (sk.skip_fp32) { p.out_re = nullptr; p.out_im = nullptr; }
-    p.t_re = sk.t_re; p.t_im = sk.t_im; p.ldt = sk.ldt;
-    p.pk_nsplit = sk.nsplit;
-    p.pkA = sk.pkA; p.pkA_kp = sk.pkA_kp; p.pkA_pitch = sk.pkA_pitch;
-    p.pkBT = sk.pkBT; p.pkBT_kp = sk.pkBT_kp; p.pkBT_pitch = sk.pkBT_pitch;
-    p.pkAT = sk.pkAT; p.pkAT_kp = sk.pkAT_kp; p.pkAT_pitch = sk.pkAT_pitch;
-    p.kM = M;
-    if (sk.skip_fp32 && beta != 0.0f) return set_err(c, APF_EINVAL, "tc_gemm: beta needs the fp32 output");
     CUtensorMap ma, mb;
     // Tile width: score the wave utilisation of 256- and 128-wide tiles.
     static int num_sms = 0;
