@@ -1,0 +1,88 @@
+"""Kernel micro-benchmarks (CUDA-event timings of single library kernels):
+
+    python -m paper_2306_09257_gb300.kernelbench gemm M N K [nsplit]   # complex M x K @ K x N on tcgen05
+    python -m paper_2306_09257_gb300.kernelbench inv N [leaf]          # mixed inversion of a slab-like block
+
+They drive the library's test hooks (apf_debug_cgemm, apf_debug_inv32) on
+seeded random inputs; used for the ncu captures summarised under profiles/.
+"""
+from __future__ import annotations
+
+import ctypes
+import sys
+
+import numpy as np
+import torch
+
+from . import apf
+
+
+def _hooks():
+    L = apf.load_library()
+    f = ctypes.c_void_p
+    L.apf_debug_cgemm.argtypes = [f, ctypes.c_int, ctypes.c_int, ctypes.c_int] + [f] * 6 + [ctypes.c_int]
+    L.apf_debug_inv32.argtypes = [f, ctypes.c_int, f, f, ctypes.c_int]
+    return L
+
+
+def gemm(m, n, k, nsplit=2, reps=3):
+    L = _hooks()
+    s = apf.Solver(0, "mixed")
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn(m, k, dtype=torch.complex64, device="cuda", generator=g)
+    B = torch.randn(k, n, dtype=torch.complex64, device="cuda", generator=g)
+    Ar, Ai, Br, Bi = A.real.contiguous(), A.imag.contiguous(), B.real.contiguous(), B.imag.contiguous()
+    Cr = torch.empty(m, n, device="cuda")
+    Ci = torch.empty(m, n, device="cuda")
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rc = L.apf_debug_cgemm(s._h, m, n, k, Ar.data_ptr(), Ai.data_ptr(), Br.data_ptr(), Bi.data_ptr(),
+                               Cr.data_ptr(), Ci.data_ptr(), nsplit)
+        e1.record()
+        torch.cuda.synchronize()
+        if rc:
+            raise apf.APFError(rc, L.apf_last_error(s._h).decode())
+        ts.append(e0.elapsed_time(e1))
+    print(f"gemm {m}x{n}x{k} nsplit {nsplit}: {min(ts):.3f} ms incl. operand packing "
+          f"({8.0 * m * n * k / (min(ts) * 1e-3) / 1e12:.1f} complex TFLOP/s)")
+
+
+def inv(n, leaf=128, reps=3):
+    L = _hooks()
+    s = apf.Solver(0, "mixed")
+    s.set_grid(n, 16, 4, 4, 8.0)
+    s.set_eps(np.full((1, n), 1.5), 2.25, 1.0)
+    s.set_channels([0], [0])
+    g = torch.Generator(device="cuda").manual_seed(n)
+    P = torch.randn(n, n, dtype=torch.complex64, device="cuda", generator=g) * (0.3 / n ** 0.5)
+    X = P + P.T
+    idx = torch.arange(n, device="cuda")
+    X[idx, idx] += 3.6 + 0.2j
+    X[idx, (idx + 1) % n] -= 1
+    X[idx, (idx - 1) % n] -= 1
+    ts = []
+    for _ in range(reps):
+        re, im = X.real.contiguous(), X.imag.contiguous()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rc = L.apf_debug_inv32(s._h, n, re.data_ptr(), im.data_ptr(), leaf)
+        e1.record()
+        torch.cuda.synchronize()
+        if rc:
+            raise apf.APFError(rc, L.apf_last_error(s._h).decode())
+        ts.append(e0.elapsed_time(e1))
+    Xi = torch.complex(re, im)
+    res = (torch.linalg.norm(Xi @ X - torch.eye(n, device="cuda", dtype=X.dtype)) / n ** 0.5).item()
+    print(f"inv {n} leaf {leaf}: {min(ts):.3f} ms, rms residual {res:.2e}")
+
+
+if __name__ == "__main__":
+    a = sys.argv[1:]
+    if a and a[0] == "gemm":
+        gemm(*[int(x) for x in a[1:4]], *([int(a[4])] if len(a) > 4 else []))
+    elif a and a[0] == "inv":
+        inv(*[int(x) for x in a[1:]])
+    else:
+        print(__doc__)
