@@ -1,6 +1,9 @@
-// Diagonal-block inversion shared by the float64 and the mixed path:
-// Gauss-Jordan elimination with partial (row) pivoting of one NB x NB block
-// in shared memory.  Thread t owns row t/4 and the columns sub + 4q
+// Diagonal-block inversion shared by the float64 and the mixed path.
+// (1) leaf_gj / leaf_gj_regs: Gauss-Jordan elimination with partial (row)
+// pivoting of one NB x NB block.  (2) leaf128_recursive: the mixed path's
+// 128 x 128 blocks, by the 2x2 Schur recursion in shared memory down to
+// 32 x 32 Gauss-Jordan leaves held in registers.
+// In (1), for the shared-memory form:  Thread t owns row t/4 and the columns sub + 4q
 // (sub = t%4), so the 4 threads of a row sit in adjacent lanes and the
 // pivot-row reads are conflict-free; rows are padded by 4 elements.
 // Row interchanges of the sweep become column interchanges of the inverse,
@@ -354,5 +357,250 @@ __device__ void leaf_gj_regs2(float *re, float *im, long long ld, int *flags) {
         long long g = (long long)r * ld + piv[sub + 4 * q];
         re[g] = a[q].x;
         im[g] = a[q].y;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// In-CTA recursive inverse of a 128 x 128 complex-symmetric fp32 block.
+// The block stays in shared memory; the 2x2 Schur recursion of the global
+// inversion (T = C Ai, D -= T B, D <- D^-1, V = D T, A += T^T V, C = -V,
+// B = -V^T) runs down to 32 x 32 diagonal blocks, which are inverted by
+// pivoted Gauss-Jordan on 4 warps with the rows in registers.  The products
+// are CTA-wide fp32 GEMMs from shared memory.  512 threads, one CTA per block.
+// ---------------------------------------------------------------------------
+namespace rec {
+constexpr int NT = 512;
+constexpr int P128 = 130, P64 = 66, P32 = 34;  // padded pitches (float2)
+
+__device__ __forceinline__ void bar4() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// C = (ACC ? C : 0) + sgn * op(A) B, all H x H (H = 32 or 64), in shared memory
+// (every block offset and pitch even, so column pairs are 16-byte aligned).
+// Thread (rt, ct) computes rows rt + i * RT (i < RB) and the column pairs
+// 2 (ct + q * CT) (q < NP), with the operands of step k + 1 loaded while
+// step k is multiplied.
+template <int H, bool TRANS_A, bool ACC>
+__device__ void gemm(const float2 *A, int lda, const float2 *B, int ldb, float2 *C, int ldc, float sgn) {
+    constexpr int CT = 16;                 // column-pair threads
+    constexpr int RT = NT / CT;            // row threads (32)
+    constexpr int RB = H / RT;             // rows per thread (2 for H = 64, 1 for H = 32)
+    constexpr int NP = H / (2 * CT);       // column pairs per thread (2 or 1)
+    const int t = threadIdx.x;
+    const int rt = t / CT, ct = t % CT;
+    float2 acc[RB][2 * NP];
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int u = 0; u < 2 * NP; ++u) acc[i][u] = make_float2(0.f, 0.f);
+    auto lda_ = [&](int k, int i) { const int r = rt + i * RT; return TRANS_A ? A[k * lda + r] : A[r * lda + k]; };
+    auto ldb_ = [&](int k, int q) { return *reinterpret_cast<const float4 *>(B + k * ldb + 2 * (ct + q * CT)); };
+    float2 a[RB];
+    float4 b[NP];
+#pragma unroll
+    for (int i = 0; i < RB; ++i) a[i] = lda_(0, i);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) b[q] = ldb_(0, q);
+#pragma unroll 2
+    for (int k = 0; k < H; ++k) {
+        float2 an[RB];
+        float4 bn[NP];
+        const int kn = k + 1 < H ? k + 1 : k;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) an[i] = lda_(kn, i);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) bn[q] = ldb_(kn, q);
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const float2 b0 = make_float2(b[q].x, b[q].y), b1 = make_float2(b[q].z, b[q].w);
+                float2 &c0 = acc[i][2 * q], &c1 = acc[i][2 * q + 1];
+                c0.x = fmaf(a[i].x, b0.x, fmaf(-a[i].y, b0.y, c0.x));
+                c0.y = fmaf(a[i].x, b0.y, fmaf(a[i].y, b0.x, c0.y));
+                c1.x = fmaf(a[i].x, b1.x, fmaf(-a[i].y, b1.y, c1.x));
+                c1.y = fmaf(a[i].x, b1.y, fmaf(a[i].y, b1.x, c1.y));
+            }
+#pragma unroll
+        for (int i = 0; i < RB; ++i) a[i] = an[i];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) b[q] = bn[q];
+    }
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            float4 *c = reinterpret_cast<float4 *>(C + (rt + i * RT) * ldc + 2 * (ct + q * CT));
+            float4 v = make_float4(sgn * acc[i][2 * q].x, sgn * acc[i][2 * q].y, sgn * acc[i][2 * q + 1].x,
+                                   sgn * acc[i][2 * q + 1].y);
+            if (ACC) {
+                const float4 o = *c;
+                v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+            }
+            *c = v;
+        }
+}
+
+// Pivoted Gauss-Jordan inverse of a 32 x 32 block (pitch ld) by warps 0..3:
+// lane i holds row i, warp w the columns 8w..8w+7, in registers.  Pivot rows
+// are not swapped: step k takes the unused row p_k with the largest
+// |a[p][k]| and eliminates column k from every other row, so that at the end
+// storage row r holds row ipiv[r] of the inverse with its columns in pivot
+// order: inv[ipiv[r]][p_c] = a[r][c].
+// After each step every warp also stores its columns to a copy in shared
+// memory (two copies, alternating by step), and the warp owning the next
+// pivot column picks the pivot with one warp max-reduction over the key
+// (|a[i][k]|^2 with its five low mantissa bits replaced by 31 - i, so ties go
+// to the lowest row); after the step's one 128-thread barrier each warp reads
+// the pivot row and column from the copy.  `scr` holds 2 x 32 x LEAF_SP
+// float2, 16-byte aligned.
+constexpr int LEAF_SP = 34;
+
+static __device__ void leaf32(float2 *a, int ld, float2 *scr, int *flags) {
+    __shared__ int pp[2], piv[32];
+    if (threadIdx.x >= 128) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float2 x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = a[lane * ld + 8 * w + j];
+    // store this warp's columns to copy `b`; the owner of column k picks its pivot
+    auto stage = [&](int b, int k, bool used) {
+        float4 *dst = reinterpret_cast<float4 *>(scr + (b * 32 + lane) * LEAF_SP + 8 * w);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dst[j] = make_float4(x[2 * j].x, x[2 * j].y, x[2 * j + 1].x, x[2 * j + 1].y);
+        if (w == (k >> 3)) {
+            const int kl = k & 7;
+            const float2 s0 = (kl & 1) ? x[1] : x[0], s1 = (kl & 1) ? x[3] : x[2];
+            const float2 s2 = (kl & 1) ? x[5] : x[4], s3 = (kl & 1) ? x[7] : x[6];
+            const float2 t0 = (kl & 2) ? s1 : s0, t1 = (kl & 2) ? s3 : s2;
+            const float2 fk = (kl & 4) ? t1 : t0;
+            const unsigned bits = __float_as_uint(fk.x * fk.x + fk.y * fk.y);
+            const unsigned key = used ? 0u : ((bits & ~31u) | (unsigned)(31 - lane));
+            const unsigned best = __reduce_max_sync(0xffffffffu, key);
+            if (lane == 0) {
+                const int p = 31 - (int)(best & 31u);
+                pp[b] = p;
+                piv[k] = p;
+            }
+        }
+    };
+    bool used = false;
+    int mystep = 0;
+    stage(0, 0, false);
+    bar4();
+    for (int k = 0; k < 32; ++k) {
+        const int buf = k & 1;
+        const int p = pp[buf];
+        const float2 *cur = scr + buf * 32 * LEAF_SP;
+        const float2 fk = cur[lane * LEAF_SP + k], d = cur[p * LEAF_SP + k];
+        float2 rr[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 q = reinterpret_cast<const float4 *>(cur + p * LEAF_SP + 8 * w)[j];
+            rr[2 * j] = make_float2(q.x, q.y);
+            rr[2 * j + 1] = make_float2(q.z, q.w);
+        }
+        const float den = d.x * d.x + d.y * d.y;
+        if (threadIdx.x == 0 && (!(den > 0.f) || !isfinite(den))) atomicOr(flags, FLAG_SINGULAR);
+        const float rd = __fdividef(1.f, den);
+        const float2 inv = make_float2(d.x * rd, -d.y * rd);
+        const bool isp = lane == p;
+        if (isp) { used = true; mystep = k; }
+        // pivot row: x <- x * inv; other rows: x <- x - f * (pivot row * inv)
+        const float2 fe = isp ? make_float2(-1.f, 0.f) : fk;
+        const float keep = isp ? 0.f : 1.f;
+        const float2 ck = make_float2(-(fe.x * inv.x - fe.y * inv.y), -(fe.x * inv.y + fe.y * inv.x));
+        const bool own = w == (k >> 3);
+        const int kl = k & 7;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float2 r = rr[j];
+            const float2 n = make_float2(r.x * inv.x - r.y * inv.y, r.x * inv.y + r.y * inv.x);
+            float2 v;
+            v.x = fmaf(keep, x[j].x, -(fe.x * n.x - fe.y * n.y));
+            v.y = fmaf(keep, x[j].y, -(fe.x * n.y + fe.y * n.x));
+            x[j] = (own && j == kl) ? ck : v;
+        }
+        if (k + 1 < 32) stage(buf ^ 1, k + 1, used);
+        bar4();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[mystep * ld + piv[8 * w + j]] = x[j];
+    bar4();
+}
+
+// Symmetric 2x2 recursion on the n x n block at `a` (n = 32 or 64) with
+// temporaries T, V (pitch P32) and the leaf scratch W.
+template <int N>
+__device__ void inv_sym(float2 *a, int ld, float2 *T, float2 *V, float2 *W, int *flags) {
+    if constexpr (N == 32) {
+        leaf32(a, ld, W, flags);
+        __syncthreads();
+    } else {
+        constexpr int H = N / 2;
+        float2 *A = a, *B = a + H, *C = a + H * ld, *D = a + H * ld + H;
+        inv_sym<H>(A, ld, nullptr, nullptr, W, flags);
+        gemm<H, false, false>(C, ld, A, ld, T, P32, 1.f);         // T = C Ai
+        __syncthreads();
+        gemm<H, false, true>(T, P32, B, ld, D, ld, -1.f);          // D -= T B
+        __syncthreads();
+        inv_sym<H>(D, ld, nullptr, nullptr, W, flags);
+        gemm<H, false, false>(D, ld, T, P32, V, P32, 1.f);         // V = Si T
+        __syncthreads();
+        gemm<H, true, true>(T, P32, V, P32, A, ld, 1.f);           // A += T^T V
+        for (int e = threadIdx.x; e < H * H; e += NT) {            // C = -V, B = -V^T
+            const int r = e / H, cc = e % H;
+            const float2 v = V[r * P32 + cc];
+            C[r * ld + cc] = make_float2(-v.x, -v.y);
+            B[cc * ld + r] = make_float2(-v.x, -v.y);
+        }
+        __syncthreads();
+    }
+}
+}  // namespace rec
+
+constexpr int rec_smem_bytes() {
+    return (128 * rec::P128 + 2 * 64 * rec::P64 + 2 * 32 * rec::P32) * 8;
+}
+
+static __device__ void leaf128_recursive(float *re, float *im, long long ld, int *flags) {
+    extern __shared__ __align__(16) unsigned char rec_smem[];
+    float2 *M = reinterpret_cast<float2 *>(rec_smem);
+    float2 *T64 = M + 128 * rec::P128, *V64 = T64 + 64 * rec::P64;
+    float2 *T32 = V64 + 64 * rec::P64, *V32 = T32 + 32 * rec::P32;
+    for (int e = threadIdx.x; e < 128 * 128; e += rec::NT) {
+        const int r = e >> 7, c = e & 127;
+        const long long g = (long long)r * ld + c;
+        M[r * rec::P128 + c] = make_float2(re[g], im[g]);
+    }
+    __syncthreads();
+    // 128: split into 64 blocks (temps T64/V64), the 64 blocks use T32/V32
+    {
+        constexpr int H = 64;
+        float2 *A = M, *B = M + H, *C = M + H * rec::P128, *D = M + H * rec::P128 + H;
+        const int ld0 = rec::P128;
+        rec::inv_sym<64>(A, ld0, T32, V32, V64, flags);
+        rec::gemm<H, false, false>(C, ld0, A, ld0, T64, rec::P64, 1.f);
+        __syncthreads();
+        rec::gemm<H, false, true>(T64, rec::P64, B, ld0, D, ld0, -1.f);
+        __syncthreads();
+        rec::inv_sym<64>(D, ld0, T32, V32, V64, flags);
+        rec::gemm<H, false, false>(D, ld0, T64, rec::P64, V64, rec::P64, 1.f);
+        __syncthreads();
+        rec::gemm<H, true, true>(T64, rec::P64, V64, rec::P64, A, ld0, 1.f);
+        for (int e = threadIdx.x; e < H * H; e += rec::NT) {
+            const int r = e / H, cc = e % H;
+            const float2 v = V64[r * rec::P64 + cc];
+            C[r * ld0 + cc] = make_float2(-v.x, -v.y);
+            B[cc * ld0 + r] = make_float2(-v.x, -v.y);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < 128 * 128; e += rec::NT) {
+        const int r = e >> 7, c = e & 127;
+        const long long g = (long long)r * ld + c;
+        const float2 v = M[r * rec::P128 + c];
+        re[g] = v.x;
+        im[g] = v.y;
     }
 }

@@ -295,6 +295,10 @@ __global__ void __launch_bounds__(NB * 4) k_leaf32r(float *re, float *im, long l
     leaf_gj_regs<NB>(re, im, ld, flags);
 }
 
+__global__ void __launch_bounds__(512) k_leaf128rec(float *re, float *im, long long ld, int *flags) {
+    leaf128_recursive(re, im, ld, flags);
+}
+
 template <int NB>
 __global__ void __launch_bounds__(NB * 4) k_leaf32r2(float *re, float *im, long long ld, int *flags) {
     leaf_gj_regs2<NB>(re, im, ld, flags);
@@ -525,12 +529,16 @@ int leaf_size(const MixedWork *w) { return w->leaf; }
 int inv32(apf_ctx *c, const PV &X, int n, float *Tre, float *Tim, float *Vre, float *Vim, cudaStream_t s) {
     MixedWork *w = c->mw;
     if (n <= leaf_size(w)) {
+        // 128 blocks: in-CTA Schur recursion over 32 x 32 Gauss-Jordan leaves
+        // (default); variants 1-3 are the single-level Gauss-Jordan kernels.
         if (n == 128 && w->leaf_variant == 1)
             APF_LAUNCH(c, k_leaf32r2<128>, 1, 512, 0, s, X.re, X.im, X.ld, c->d_flags);
         else if (n == 128 && w->leaf_variant == 2)
             APF_LAUNCH(c, k_leaf32<128>, 1, 512, leaf_smem_bytes<128>(8), s, X.re, X.im, X.ld, c->d_flags);
-        else if (n == 128)
+        else if (n == 128 && w->leaf_variant == 3)
             APF_LAUNCH(c, k_leaf32r<128>, 1, 512, 0, s, X.re, X.im, X.ld, c->d_flags);
+        else if (n == 128)
+            APF_LAUNCH(c, k_leaf128rec, 1, 512, rec_smem_bytes(), s, X.re, X.im, X.ld, c->d_flags);
         else if (n == 64 && w->leaf_variant == 1)
             APF_LAUNCH(c, k_leaf32r2<64>, 1, 256, 0, s, X.re, X.im, X.ld, c->d_flags);
         else if (n == 64)
@@ -625,6 +633,7 @@ void mixed_init_attrs() {
     cudaFuncSetAttribute(k_leaf_inv32, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * (int)sizeof(float2));
     cudaFuncSetAttribute(k_leaf32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_smem_bytes<128>(8));
     cudaFuncSetAttribute(k_leaf32<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, leaf_smem_bytes<64>(8));
+    cudaFuncSetAttribute(k_leaf128rec, cudaFuncAttributeMaxDynamicSharedMemorySize, rec_smem_bytes());
     cudaFuncSetAttribute(k_circ_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * (int)sizeof(double2));
 }
 

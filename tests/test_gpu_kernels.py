@@ -54,7 +54,9 @@ def test_tc_cgemm_against_torch(env, shape, nsplit):
     assert err < TOL[nsplit], err
 
 
-@pytest.mark.parametrize("n,leaf", [(64, 64), (256, 64), (512, 128), (1024, 128)])
+# leaf = block size + 1000 * leaf kernel variant (128 blocks: 0 in-CTA Schur
+# recursion over 32 x 32 Gauss-Jordan leaves, 3 single-level Gauss-Jordan)
+@pytest.mark.parametrize("n,leaf", [(64, 64), (256, 64), (128, 128), (512, 128), (1024, 128), (1024, 3128)])
 def test_mixed_recursive_inverse(env, n, leaf):
     """Inverse of a complex-symmetric matrix shaped like a slab Schur block
     (diagonal ~4 - k^2 eps, periodic -1 neighbours, a dense symmetric
