@@ -343,10 +343,24 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 // with a cluster multicast into both CTAs' shared memory, and each MMA
 // completion is committed to the stage barriers of both CTAs (a stage is
 // refilled only when both have consumed it).  Halves the B traffic per SM.
-template <int BN, int STAGES>
+// FUSED (two split planes only): a stage holds both planes of the A and the
+// B tile of one k block, and the three retained plane products (x0 y0, x0 y1,
+// x1 y0) are issued from it, so each plane tile is loaded once instead of
+// once per product that uses it (4 tile loads per k block instead of 6).
+template <int BN, int STAGES, bool FUSED>
+struct McLayout {
+    static constexpr int PL = FUSED ? 2 : 1;  // planes per operand per stage
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE = PL * (A_BYTES + B_BYTES);
+    static constexpr int BAR = STAGES * STAGE;
+    static constexpr int TOTAL = BAR + (2 * STAGES + 4) * 8 + 16 + 1024;
+};
+
+template <int BN, int STAGES, bool FUSED>
 __global__ void __launch_bounds__(192, 1)
     k_tc_gemm_mc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
-    using L = Layout<BN, STAGES>;
+    using L = McLayout<BN, STAGES, FUSED>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + L::BAR);
@@ -361,7 +375,7 @@ __global__ void __launch_bounds__(192, 1)
     const int Mt = (p.M + BM - 1) / BM, Mp = (Mt + 1) / 2, Nt = (p.N + BN - 1) / BN;
     const int npairs = Mp * Nt;
     const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
-    const int total = p.nseg * p.kblocks;
+    const int total = FUSED ? p.kblocks : p.nseg * p.kblocks;
     constexpr int HALF = BN / 2;
     constexpr int HALF_BYTES = HALF * BK * 2;
 
@@ -399,14 +413,26 @@ __global__ void __launch_bounds__(192, 1)
                 for (int kk = 0; kk < total; ++kk, ++it) {
                     const int s = it % STAGES, r = it / STAGES;
                     if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) { ok = false; break; }
-                    const int seg = kk / p.kblocks, kb = kk - seg * p.kblocks;
-                    const int pa = (p.seg_pairs >> (4 * seg + 2)) & 3, pb = (p.seg_pairs >> (4 * seg)) & 3;
                     uint8_t *sa = smem + s * L::STAGE;
-                    uint8_t *sb = sa + L::A_BYTES;
-                    mbar_expect_tx(&full[s], L::A_BYTES + L::B_BYTES);
-                    tma_load_3d(sa, &tmA, &full[s], kb * BK, m0, pa);
-                    tma_load_3d_mc(sb + rank * HALF_BYTES, &tmB, &full[s], kb * BK, n0 + rank * HALF, pb,
-                                   (uint16_t)3);
+                    if constexpr (FUSED) {
+                        // [A plane 0 | A plane 1 | B plane 0 | B plane 1]
+                        uint8_t *sb = sa + 2 * L::A_BYTES;
+                        mbar_expect_tx(&full[s], L::STAGE);
+                        tma_load_3d(sa, &tmA, &full[s], kk * BK, m0, 0);
+                        tma_load_3d(sa + L::A_BYTES, &tmA, &full[s], kk * BK, m0, 1);
+                        tma_load_3d_mc(sb + rank * HALF_BYTES, &tmB, &full[s], kk * BK, n0 + rank * HALF, 0,
+                                       (uint16_t)3);
+                        tma_load_3d_mc(sb + L::B_BYTES + rank * HALF_BYTES, &tmB, &full[s], kk * BK,
+                                       n0 + rank * HALF, 1, (uint16_t)3);
+                    } else {
+                        const int seg = kk / p.kblocks, kb = kk - seg * p.kblocks;
+                        const int pa = (p.seg_pairs >> (4 * seg + 2)) & 3, pb = (p.seg_pairs >> (4 * seg)) & 3;
+                        uint8_t *sb = sa + L::A_BYTES;
+                        mbar_expect_tx(&full[s], L::A_BYTES + L::B_BYTES);
+                        tma_load_3d(sa, &tmA, &full[s], kb * BK, m0, pa);
+                        tma_load_3d_mc(sb + rank * HALF_BYTES, &tmB, &full[s], kb * BK, n0 + rank * HALF, pb,
+                                       (uint16_t)3);
+                    }
                     issued = it + 1;
                 }
             }
@@ -432,11 +458,25 @@ __global__ void __launch_bounds__(192, 1)
                     if (!mbar_wait(&full[s], r & 1, abort_flag)) { ok = false; break; }
                     fence_after();
                     const uint32_t sa = smem_u32(smem + s * L::STAGE);
-                    const uint32_t sb = sa + L::A_BYTES;
+                    if constexpr (FUSED) {
+                        const uint32_t sa1 = sa + L::A_BYTES, sb0 = sa + 2 * L::A_BYTES, sb1 = sb0 + L::B_BYTES;
 #pragma unroll
-                    for (int k4 = 0; k4 < BK / 16; ++k4)
-                        mma_bf16(acc, sw128_desc(sa + k4 * 32), sw128_desc(sb + k4 * 32), idesc,
-                                 (kk > 0 || k4 > 0) ? 1u : 0u);
+                        for (int k4 = 0; k4 < BK / 16; ++k4)
+                            mma_bf16(acc, sw128_desc(sa + k4 * 32), sw128_desc(sb0 + k4 * 32), idesc,
+                                     (kk > 0 || k4 > 0) ? 1u : 0u);
+#pragma unroll
+                        for (int k4 = 0; k4 < BK / 16; ++k4)
+                            mma_bf16(acc, sw128_desc(sa + k4 * 32), sw128_desc(sb1 + k4 * 32), idesc, 1u);
+#pragma unroll
+                        for (int k4 = 0; k4 < BK / 16; ++k4)
+                            mma_bf16(acc, sw128_desc(sa1 + k4 * 32), sw128_desc(sb0 + k4 * 32), idesc, 1u);
+                    } else {
+                        const uint32_t sb = sa + L::A_BYTES;
+#pragma unroll
+                        for (int k4 = 0; k4 < BK / 16; ++k4)
+                            mma_bf16(acc, sw128_desc(sa + k4 * 32), sw128_desc(sb + k4 * 32), idesc,
+                                     (kk > 0 || k4 > 0) ? 1u : 0u);
+                    }
                     mma_commit_mc(&empty[s], (uint16_t)3);
                 }
                 if (!ok) break;
@@ -535,12 +575,16 @@ uint32_t tc_seg_pairs(int nsplit, int *nseg) {
 void tc_init_attrs() {
     set_attr<256, 4>();
     set_attr<128, 6>();
-    cudaFuncSetAttribute(k_tc_gemm_mc<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<256, 4>::TOTAL);
-    cudaFuncSetAttribute(k_tc_gemm_mc<256, 4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
+    cudaFuncSetAttribute(k_tc_gemm_mc<256, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         McLayout<256, 4, false>::TOTAL);
+    cudaFuncSetAttribute(k_tc_gemm_mc<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         McLayout<256, 2, true>::TOTAL);
 }
 
 // 0: one CTA per tile; 1: two-CTA clusters sharing B tiles (wide tiles only).
 int g_tc_cluster_mode = 1;
+// Cluster kernel with both split planes per stage (two-plane products only).
+int g_tc_fused = 1;
 
 int tc_init() { return ensure_encode() ? APF_OK : APF_ECUDA; }
 
@@ -608,7 +652,13 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(2 * ncl));
         cfg.blockDim = dim3(192);
-        cfg.dynamicSmemBytes = smem_wide;
+        static int fused_env = -1;
+        if (fused_env < 0) {
+            const char *e = getenv("APF_GEMM_FUSED");  // tuning knob; default on
+            fused_env = (e && e[0] == '0') ? 0 : 1;
+        }
+        const bool fused = (nsplit == 2) && g_tc_fused && fused_env;
+        cfg.dynamicSmemBytes = fused ? McLayout<256, 2, true>::TOTAL : McLayout<256, 4, false>::TOTAL;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -617,7 +667,8 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_gemm_mc<256, 4>, ma, mbh, p);
+        cudaError_t e = fused ? cudaLaunchKernelEx(&cfg, k_tc_gemm_mc<256, 2, true>, ma, mbh, p)
+                              : cudaLaunchKernelEx(&cfg, k_tc_gemm_mc<256, 4, false>, ma, mbh, p);
         if (e != cudaSuccess) return check_cuda(c, e, "cluster GEMM launch");
         c->launches++;
     } else if (wide) {

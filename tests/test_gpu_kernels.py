@@ -26,8 +26,9 @@ def planar(torch, z):
     return z.real.float().contiguous(), z.imag.float().contiguous()
 
 
-# (m, n, k): aligned, ragged m/n/k, and a size that fills the GPU with wide tiles.
-SHAPES = [(128, 256, 64), (200, 130, 96), (37, 300, 40), (1024, 2048, 512)]
+# (m, n, k): aligned, ragged m/n/k, and sizes that take the wide-tile two-CTA
+# cluster kernel (aligned, and ragged in m, n and k).
+SHAPES = [(128, 256, 64), (200, 130, 96), (37, 300, 40), (1024, 2048, 512), (1000, 3000, 264)]
 TOL = {1: 1.5e-2, 2: 1e-4, 3: 3e-5}  # 3 planes: limited by the tensor-core fp32 accumulation
 
 
