@@ -61,6 +61,7 @@ def test_tiny_S_and_grad(apf, prec, seed):
     assert np.array_equal(mi, pb.inputs()) and np.array_equal(mo, pb.outputs())
     S, f, g = s.solve_S_grad("splitter", orders, 0.18)
     ts, tg = TOL[prec]
+    print(f"parity tiny seed {seed} {prec}: err S {rel(S, sol.S):.2e}, err grad {rel(g, g_ref):.2e}")
     assert rel(S, sol.S) <= ts
     assert rel(g, g_ref) <= tg
     assert abs(f - f_ref) <= ts * abs(f_ref) * 10
@@ -121,6 +122,7 @@ def test_mid_against_golden(apf, prec):
     s = A.solver_for_workload(w, eps, precision=prec)
     S, f, g = s.solve_S_grad("splitter", [-2, -1, 0, 1, 2], 0.18)
     ts, tg = TOL[prec]
+    print(f"parity mid {prec}: err S {rel(S, ref['S']):.2e}, err grad {rel(g, ref['grad']):.2e}")
     assert rel(S, ref["S"]) <= ts, rel(S, ref["S"])
     assert rel(g, ref["grad"]) <= tg, rel(g, ref["grad"])
 
