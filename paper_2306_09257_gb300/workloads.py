@@ -85,3 +85,30 @@ def filtered_threshold_eps(h: int, nx: int, seed: int, sigma: float = 3.0,
     b = (g > 0.5).astype(np.float64)
     rho = ndimage.uniform_filter(b, size=ramp_px, mode=("reflect", "wrap"))
     return (eps_min + contrast * rho).astype(np.float64)
+
+
+def ridge_edges(nx: int, n_ridges: int, seed: int, mirror: bool = True, min_gap: float = 2.0) -> np.ndarray:
+    """Seeded ridge edge positions (pixels, measured from the mirror plane x = nx/2).
+
+    The paper's metasurface (Sec. 3) is parametrized by the two edge positions
+    of each ridge; with mirror symmetry only the ridges of one half period are
+    free.  Returns 2 n_ridges sorted positions t_0 < t_1 < ... in
+    [-nx/2, 0] (mirror) or [-nx/2, nx/2] (no mirror); ridge i spans
+    [t_{2i}, t_{2i+1}].  Neighbouring edges (ridge widths and gaps) are at least
+    `min_gap` apart, as are the outermost edges from the interval ends, so the
+    mirrored and the periodic neighbours never overlap.
+    """
+    lo, hi = -nx / 2.0, (0.0 if mirror else nx / 2.0)
+    n = 2 * n_ridges
+    free = (hi - lo) - (n + 1) * min_gap
+    if free <= 0:
+        raise ValueError("too many ridges for the interval and gap")
+    u = np.sort(np.random.default_rng(seed).uniform(0.0, free, n))
+    return lo + min_gap * (np.arange(n) + 1) + u
+
+
+def ridge_count(w: "Workload") -> int:
+    """Ridges per half period for a workload: one ridge per ~0.64 wavelength,
+    the paper's 80-ridge, 25.5-wavelength beam splitter (Sec. 3) scaled to the
+    grid's period."""
+    return max(1, int(round(w.nx / (2 * 0.64 * w.lambda_px))))
