@@ -5,7 +5,10 @@ A step is one full pass of the hot path for one permittivity map: per-mode
 boundary elimination, slab block-Schur elimination, forward + adjoint field
 sweeps with float64 refinement, S readout, beam-splitter objective (Eq. 5,
 relative orders -2..2, target 0.18) and the adjoint gradient for every slab
-pixel.  Inputs are synthetic filtered-threshold metasurfaces (seeded).
+pixel.  Inputs are synthetic filtered-threshold metasurfaces (seeded), or with
+`--design ridges` mirror-symmetric ridge metasurfaces parametrized by their
+edge positions (paper Sec. 3): each step then also builds the slab from the
+edges and carries the gradient on to the edges.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
@@ -35,6 +38,7 @@ from paper_2306_09257_gb300 import workloads as W  # noqa: E402
 METRIC = "S+grad evals/s, mixed vs FP64 on 1 GB300 at stated err; % of tensor peak"
 ORDERS = [-2, -1, 0, 1, 2]
 TARGET = 0.18
+EPS_RIDGE, EPS_BG = 13.69, 1.0  # amorphous-silicon ridges in air (Sec. 3: n = 3.70)
 WL = {"mid": W.MID, "large": W.LARGE, "xlarge": W.XLARGE, "tiny": W.TINY}
 
 
@@ -52,6 +56,8 @@ def args_parse():
     p.add_argument("--refine-tol", type=float, default=1e-7,
                    help="refinement tolerance (max column ||r||/||R||) of the mixed solves; 1e-7 keeps S within "
                         "~1e-7 and grad f within ~1e-6 of the float64 path, inside the stated 1e-6 / 1e-5")
+    p.add_argument("--design", default="filtered", choices=["filtered", "ridges"],
+                   help="permittivity maps: filtered-threshold pixels or ridge edge positions")
     p.add_argument("--concurrent", type=int, default=8,
                    help="independent designs in flight per GPU (one context + stream + host thread each)")
     return p.parse_args()
@@ -212,23 +218,47 @@ def main():
     dev = torch.device("cuda", local)
     B = max(1, a.concurrent)
     nseeds = 4
-    eps_host = [[w.eps_slab(sd) for sd in row] for row in replicas.replica_seeds(rank, B, nseeds)]
+    ridges = a.design == "ridges"
+    seeds = replicas.replica_seeds(rank, B, nseeds)
+    if ridges:
+        nr = W.ridge_count(w)
+        eps_host = [[W.ridge_edges(w.nx, nr, sd, mirror=True) for sd in row] for row in seeds]
+    else:
+        eps_host = [[w.eps_slab(sd) for sd in row] for row in seeds]
     eps_dev = [[torch.tensor(e, device=dev) for e in row] for row in eps_host]
-    solvers = [apf.solver_for_workload(w, eps_host[b][0], precision="mixed", device=local) for b in range(B)]
+
+    def set_design(sv, x):
+        """x: a permittivity slab, or ridge edge positions with --design ridges."""
+        if ridges:
+            sv.set_ridges(x, w.h, EPS_RIDGE, EPS_BG, w.eps_sub, w.eps_clad, mirror=True, j0=w.j0, eps_out=False)
+        else:
+            sv.set_eps(x, w.eps_sub, w.eps_clad, j0=w.j0)
+
+    solvers = []
+    for b in range(B):
+        sv = apf.Solver(device=local, precision="mixed")
+        sv.set_grid(w.nx, w.ny, w.npml, w.npml, w.lambda_px)
+        set_design(sv, eps_host[b][0])
+        sv.set_channels(None, None)
+        solvers.append(sv)
     if a.refine_tol is not None:
         for sv in solvers:
-            sv.set_refinement(a.refine_tol, 8)
+            sv.set_refinement(a.refine_tol, 40)
     s = solvers[0]
     m_in, m_out = s.channels()
     streams = [torch.cuda.Stream(device=dev) for _ in range(B)]
     S_d = [torch.empty((len(m_out), len(m_in)), dtype=torch.complex128, device=dev) for _ in range(B)]
     g_d = [torch.empty((w.h, w.nx), dtype=torch.float64, device=dev) for _ in range(B)]
-    stats_acc = [dict(launches=0, iters=[]) for _ in range(B)]
+    ge_d = [torch.empty(len(eps_host[0][0]) if ridges else 1, dtype=torch.float64, device=dev) for _ in range(B)]
+    stats_acc = [dict(launches=0, iters=[], fallbacks=0) for _ in range(B)]
 
     def step(b, i):
         sv = solvers[b]
-        sv.set_eps(eps_dev[b][i % nseeds], w.eps_sub, w.eps_clad, j0=w.j0)
-        return sv.solve_S_grad("splitter", ORDERS, TARGET, out_S=S_d[b], out_grad=g_d[b])
+        set_design(sv, eps_dev[b][i % nseeds])
+        r = sv.solve_S_grad("splitter", ORDERS, TARGET, out_S=S_d[b], out_grad=g_d[b])
+        if ridges:
+            sv.ridge_grad(g_d[b], out=ge_d[b])
+        return r
 
     def worker(b, nsteps, start_ev, end_evs, record):
         with torch.cuda.stream(streams[b]):
@@ -240,17 +270,28 @@ def main():
                     st = solvers[b].stats()
                     stats_acc[b]["launches"] += st["kernel_launches"]
                     stats_acc[b]["iters"].append(st["refine_iters"])
+                    stats_acc[b]["fallbacks"] += st["leaf_fallbacks"]
             if end_evs is not None:
                 end_evs[b].record(streams[b])
 
     import threading
 
+    errors = []
+
+    def guarded(*args):
+        try:
+            worker(*args)
+        except BaseException as e:  # re-raised on the main thread: a failed step fails the bench
+            errors.append(e)
+
     def run_all(nsteps, start_ev=None, end_evs=None, record=False):
-        ths = [threading.Thread(target=worker, args=(b, nsteps, start_ev, end_evs, record)) for b in range(B)]
+        ths = [threading.Thread(target=guarded, args=(b, nsteps, start_ev, end_evs, record)) for b in range(B)]
         for t in ths:
             t.start()
         for t in ths:
             t.join()
+        if errors:
+            raise errors[0]
 
     for sv in solvers:
         sv.set_profiling(True)
@@ -292,24 +333,41 @@ def main():
     for i in range(a.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.set_eps(eps_host[i % nseeds], w.eps_sub, w.eps_clad, j0=w.j0)
-        S_h, f_h, g_h = s.solve_S_grad("splitter", ORDERS, TARGET)
+        set_design(s, eps_host[i % nseeds])
+        if ridges:
+            # host edges in, host S, f and df/d(edges) out; the pixel gradient stays on the device
+            S_h, f_h, _ = s.solve_S_grad("splitter", ORDERS, TARGET, out_grad=g_d[0])
+            ge_h = s.ridge_grad(g_d[0])
+        else:
+            S_h, f_h, g_h = s.solve_S_grad("splitter", ORDERS, TARGET)
         e2e_t.append(time.perf_counter() - t0)
     e2e_val = ws * 1.0 / statistics.mean(e2e_t) if e2e_t else None
-    h2d = w.h * w.nx * 8
-    d2h = len(m_in) * len(m_out) * 16 + w.h * w.nx * 8 + 8
+    if ridges:
+        ne = len(eps_host[0])
+        h2d = ne * 8
+        d2h = len(m_in) * len(m_out) * 16 + ne * 8 + 8
+    else:
+        h2d = w.h * w.nx * 8
+        d2h = len(m_in) * len(m_out) * 16 + w.h * w.nx * 8 + 8
 
     # float64 GPU path on the same workload and the mixed-vs-float64 error
     fp64 = None
     if a.fp64_steps > 0:
-        s64 = apf.solver_for_workload(w, eps_host[0], precision="fp64", device=local)
+        s64 = apf.Solver(device=local, precision="fp64")
+        s64.set_grid(w.nx, w.ny, w.npml, w.npml, w.lambda_px)
+        set_design(s64, eps_host[0])
+        s64.set_channels(None, None)
         s64.solve_S_grad("splitter", ORDERS, TARGET)  # warm-up
         t0 = time.perf_counter()
         for _ in range(a.fp64_steps):
             S64, f64v, g64 = s64.solve_S_grad("splitter", ORDERS, TARGET)
+            if ridges:
+                g64 = s64.ridge_grad(g64)
         t64 = (time.perf_counter() - t0) / a.fp64_steps
-        s.set_eps(eps_host[0], w.eps_sub, w.eps_clad, j0=w.j0)
+        set_design(s, eps_host[0])
         Sm, fm, gm = s.solve_S_grad("splitter", ORDERS, TARGET)
+        if ridges:
+            gm = s.ridge_grad(gm)
         fp64 = {"value": 1.0 / t64, "unit": "evals/s", "steps": a.fp64_steps,
                 "err_S_mixed_vs_fp64": rel(Sm, S64), "err_grad_mixed_vs_fp64": rel(gm, g64),
                 "speedup_mixed_over_fp64": value / ws * t64,
@@ -332,7 +390,12 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
-        t_eval, t_fac, t_solve, nin = cpu_oracle_sample(w, eps_host[0], a.solves)
+        if ridges:
+            import oracle as O
+            eps_cpu = O.eps_from_edges(w.nx, w.h, eps_host[0], True, EPS_RIDGE, EPS_BG)
+        else:
+            eps_cpu = eps_host[0]
+        t_eval, t_fac, t_solve, nin = cpu_oracle_sample(w, eps_cpu, a.solves)
         cpu = {"value": 1.0 / t_eval, "unit": "evals/s", "cores": 1, "kind": "oracle",
                "sample": (f"SuperLU factor ({t_fac:.1f} s, serial) + {a.solves} forward and {a.solves} adjoint "
                           f"solves ({t_solve:.3f} s each), extrapolated to 2*{nin} solves per evaluation")}
@@ -342,10 +405,14 @@ def main():
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
                 "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "npml": w.npml, "lambda_px": w.lambda_px,
-                           "h": w.h, "channels": [len(m_in), len(m_out)], "eps": "filtered-threshold, seeded",
+                           "h": w.h, "channels": [len(m_in), len(m_out)],
+                           "eps": (f"ridges: {len(eps_host[0]) // 2} per half period, mirror symmetric, eps "
+                                   f"{EPS_RIDGE}/{EPS_BG}, gradient to the {len(eps_host[0])} edge positions"
+                                   if ridges else "filtered-threshold, seeded"),
                            "objective": "beam splitter Eq. 5, orders -2..2, t=0.18",
                            "l2": f"working set {st_last['workspace_bytes'] / 1e9:.1f} GB > 129 MB L2, no flush",
                            "refine_iters": iters, "residual": st_last["residual"],
+                           "leaf_fallbacks_per_step": sum(x["fallbacks"] for x in stats_acc) / (B * a.steps),
                            "concurrent_designs_per_gpu": B,
                            "parallelism": f"replicas x{ws}, {B} independent designs per GPU"},
                 "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

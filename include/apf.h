@@ -85,6 +85,9 @@ typedef struct {
     double ms_gradient;     /* adjoint contraction */
     long long kernel_launches; /* kernels launched by the last solve */
     long long workspace_bytes; /* device bytes held by the context */
+    int leaf_fallbacks;     /* mixed mode: 128 x 128 diagonal blocks whose recursive
+                               inversion failed its self-check and were redone with
+                               pivoting over the whole block (last solve) */
 } apf_stats;
 
 /* Create a context on CUDA device `cuda_device` with APF_FP64 or
@@ -132,8 +135,39 @@ int apf_solve_S_grad(apf_ctx *ctx, int objective, const double *params, int n_pa
    solve (Eq. 1 with Eq. 3).  grad_eps: h*nx float64. */
 int apf_grad_from_gamma(apf_ctx *ctx, const double *Gamma, double *grad_eps, void *stream);
 
-/* Iterative refinement of the mixed mode: stop when max_col ||r||/||R|| <= tol
-   or after max_iters sweeps (APF_ENOCONV if still above tol). */
+/* Ridge metasurface parametrization (paper Sec. 3 and Eq. 5: the design
+   variables are the edge positions of the ridges; mirror symmetry maps the
+   free half period onto the other half, Supplement Sec. 6 frees all edges).
+   edges: n_edges float64 (host or device), positions in pixels measured from
+   the mirror plane x = nx/2, nondecreasing, ridge i = [t_2i, t_2i+1];
+   -nx/2 <= t_0 and t_last <= 0 (mirror != 0) or <= nx/2 (mirror == 0).
+   With mirror != 0 the image ridges [-t_2i+1, -t_2i] are added.  Every slab
+   row gets the profile eps_x = eps_bg + (eps_ridge - eps_bg) * (length of
+   pixel [x, x+1) covered by ridges) -- the paper does not fix the sub-pixel
+   treatment; this linear one is continuous in every edge.  The slab is then
+   set exactly as apf_set_eps(ctx, eps, j0, h, eps_sub, eps_clad) would;
+   eps_out (h*nx, host or device, may be NULL) receives it.  Requires
+   apf_set_grid; APF_EINVAL for unsorted, out-of-range or non-finite edges. */
+int apf_set_ridges(apf_ctx *ctx, const double *edges, int n_edges, int mirror,
+                   double eps_ridge, double eps_bg, int j0, int h,
+                   double eps_sub, double eps_clad, double *eps_out);
+
+/* Chain rule from a pixel gradient to the edges of the last apf_set_ridges:
+   df/dt_k = sum_{rows, x} (df/deps)[row][x] * deps_x/dt_k, where deps_x/dt_k
+   = -+(eps_ridge - eps_bg) on the pixel the edge moves into (minus for a
+   ridge's left edge, plus for its right edge) and, with mirror symmetry, on
+   the pixel its image moves into (dA/dp_k of rank h, Eq. 2 with r_k = h).
+   At an exact pixel boundary the derivative for increasing t is taken.
+   grad_eps: h*nx float64 (e.g. from apf_solve_S_grad), grad_edges: n_edges
+   float64; host or device each.  Enqueues on `stream` and synchronizes it.
+   APF_ESTATE before apf_set_ridges or after the slab was replaced. */
+int apf_ridge_grad(apf_ctx *ctx, const double *grad_eps, double *grad_edges, void *stream);
+
+/* Iterative refinement of the mixed mode: stop when max_col ||r||/||R|| <= tol,
+   after max_iters sweeps, or when the residual grew on two consecutive sweeps
+   (APF_ENOCONV if still above tol).  Defaults: tol 1e-10, max_iters 40.
+   Low-contrast slabs need 1-3 sweeps; high-contrast ones (e.g. silicon
+   ridges in air) up to ~25 to reach 1e-10. */
 int apf_set_refinement(apf_ctx *ctx, double tol, int max_iters);
 
 int apf_get_stats(const apf_ctx *ctx, apf_stats *stats);

@@ -28,7 +28,7 @@ OBJECTIVES = {"power": APF_OBJ_POWER, "splitter": APF_OBJ_SPLITTER}
 EXPORTS = ("apf_create", "apf_destroy", "apf_set_grid", "apf_set_eps", "apf_set_channels",
            "apf_get_channels", "apf_solve_S", "apf_solve_S_grad", "apf_grad_from_gamma",
            "apf_set_refinement", "apf_get_stats", "apf_set_profiling", "apf_get_profile",
-           "apf_solve_S_noalloc", "apf_last_error", "apf_version",
+           "apf_solve_S_noalloc", "apf_last_error", "apf_version", "apf_set_ridges", "apf_ridge_grad",
            "apf_sno_create", "apf_sno_destroy", "apf_sno_num_params", "apf_sno_set_params",
            "apf_sno_get_params", "apf_sno_forward", "apf_sno_gradients", "apf_sno_train_step")
 
@@ -44,7 +44,8 @@ class Stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_boundary", ctypes.c_double),
                 ("ms_eliminate", ctypes.c_double), ("ms_fields", ctypes.c_double),
                 ("ms_readout", ctypes.c_double), ("ms_gradient", ctypes.c_double),
-                ("kernel_launches", ctypes.c_longlong), ("workspace_bytes", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("workspace_bytes", ctypes.c_longlong),
+                ("leaf_fallbacks", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +90,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.apf_set_profiling.argtypes = [vp, i]
     L.apf_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
     L.apf_solve_S_noalloc.argtypes = [i, i, i, i, d, ctypes.POINTER(PML), dp, i, i, d, d, ip, i, ip, i, dp, vp]
+    L.apf_set_ridges.argtypes = [vp, dp, i, i, d, d, i, i, d, d, dp]
+    L.apf_ridge_grad.argtypes = [vp, dp, dp, vp]
     L.apf_last_error.argtypes = [vp]
     L.apf_last_error.restype = ctypes.c_char_p
     L.apf_version.argtypes = []
@@ -130,6 +133,7 @@ class Solver:
         self.precision = precision
         self.device = device
         self.nx = self.h = None
+        self.n_edges = 0
         self.version = 0  # bumped by every call that changes the stored fields
 
     def close(self):
@@ -161,6 +165,36 @@ class Solver:
                                         float(eps_sub), float(eps_clad)))
         self.h = h
         self.version += 1
+
+    def set_ridges(self, edges, h: int, eps_ridge: float, eps_bg: float, eps_sub: float, eps_clad: float,
+                   mirror: bool = True, j0: int = -1, eps_out=None):
+        """Slab permittivity from ridge edge positions (paper Sec. 3; see
+        apf_set_ridges), set as by set_eps.  Returns the h x nx slab (a new
+        host array when eps_out is None; nothing is copied out when eps_out
+        is False)."""
+        if isinstance(edges, np.ndarray) or not hasattr(edges, "data_ptr"):
+            edges = np.ascontiguousarray(edges, dtype=np.float64)
+        if eps_out is False:
+            eps, eps_p = None, None
+        else:
+            eps = np.empty((int(h), self.nx), dtype=np.float64) if eps_out is None else eps_out
+            eps_p = _ptr(eps, np.float64)
+        self._check(self._L.apf_set_ridges(self._h, _ptr(edges, np.float64), int(edges.shape[0]),
+                                           1 if mirror else 0, float(eps_ridge), float(eps_bg), int(j0), int(h),
+                                           float(eps_sub), float(eps_clad), eps_p))
+        self.h = int(h)
+        self.n_edges = int(edges.shape[0])
+        self.version += 1
+        return eps
+
+    def ridge_grad(self, grad_eps, out=None):
+        """df/d(edge positions) of the last set_ridges from a pixel gradient."""
+        if isinstance(grad_eps, np.ndarray):
+            grad_eps = np.ascontiguousarray(grad_eps, dtype=np.float64)
+        g = np.empty(self.n_edges, dtype=np.float64) if out is None else out
+        st = _stream_of(grad_eps, g)
+        self._check(self._L.apf_ridge_grad(self._h, _ptr(grad_eps, np.float64), _ptr(g, np.float64), st))
+        return g
 
     def set_channels(self, m_in: Optional[Sequence[int]] = None, m_out: Optional[Sequence[int]] = None):
         def arr(v):

@@ -1,4 +1,4 @@
-"""torch.autograd wrapper: S(eps) with the adjoint contraction as backward.
+"""torch.autograd wrappers: S(eps) and S(ridge edges) with the adjoint contraction as backward.
 
 ``scattering(eps, solver)`` returns the complex transmission matrix S for the
 slab permittivity ``eps`` (float64, shape (h, nx), CPU or CUDA).  Any real
@@ -59,6 +59,45 @@ def scattering(eps: torch.Tensor, solver: "_apf.Solver", eps_sub: float, eps_cla
     """S(eps) as a differentiable torch op (the solver keeps its grid and
     channel set; eps must have the solver's slab shape)."""
     return _Scattering.apply(eps, solver, eps_sub, eps_clad, j0)
+
+
+class _RidgeScattering(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, edges: torch.Tensor, solver: "_apf.Solver", geom: tuple):
+        e = edges.detach().to(torch.float64).contiguous()
+        solver.set_ridges(e, *geom, eps_out=False)
+        mi, mo = solver.channels()
+        S = torch.empty((len(mo), len(mi)), dtype=torch.complex128, device=edges.device)
+        solver.solve_S(out=S)
+        ctx.version = solver.version
+        ctx.save_for_backward(e)
+        ctx.solver, ctx.geom = solver, geom
+        ctx.edges_dtype = edges.dtype
+        return S
+
+    @staticmethod
+    def backward(ctx, grad_S: torch.Tensor):
+        (e,) = ctx.saved_tensors
+        solver = ctx.solver
+        if solver.version != ctx.version:
+            solver.set_ridges(e, *ctx.geom, eps_out=False)
+            mi, mo = solver.channels()
+            solver.solve_S(out=torch.empty((len(mo), len(mi)), dtype=torch.complex128, device=e.device))
+        gamma = (grad_S.conj() * 0.5).to(torch.complex128).contiguous()
+        g_eps = torch.empty((solver.h, solver.nx), dtype=torch.float64, device=e.device)
+        solver.grad_from_gamma(gamma, out=g_eps)
+        g_e = torch.empty(e.shape[0], dtype=torch.float64, device=e.device)
+        solver.ridge_grad(g_eps, out=g_e)
+        return g_e.to(ctx.edges_dtype), None, None
+
+
+def ridge_scattering(edges: torch.Tensor, solver: "_apf.Solver", h: int, eps_ridge: float, eps_bg: float,
+                     eps_sub: float, eps_clad: float, mirror: bool = True, j0: int = -1) -> torch.Tensor:
+    """S as a differentiable function of the ridge edge positions (paper
+    Sec. 3, Eq. 5's design variables): forward = apf_set_ridges + solve_S,
+    backward = the pixel adjoint contraction followed by apf_ridge_grad.  The
+    solver keeps its grid and channel set."""
+    return _RidgeScattering.apply(edges, solver, (h, eps_ridge, eps_bg, eps_sub, eps_clad, mirror, j0))
 
 
 def relative_order_mask(m_in: Sequence[int], m_out: Sequence[int], orders: Sequence[int],

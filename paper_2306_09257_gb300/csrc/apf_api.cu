@@ -46,7 +46,7 @@ GridDev make_grid(const apf_ctx *c) {
     return g;
 }
 
-static bool is_device_ptr(const void *p) {
+bool is_device_ptr(const void *p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
@@ -132,7 +132,7 @@ static double disp_q(const apf_ctx *c, int m, double eps) {
 
 extern "C" {
 
-int apf_version(void) { return (1 << 16) | 0; }
+int apf_version(void) { return (1 << 16) | 1; }
 
 int apf_create(apf_ctx **out, int cuda_device, int precision) {
     if (!out) return set_err(nullptr, APF_EINVAL, "apf_create: out is NULL");
@@ -177,6 +177,7 @@ void apf_destroy(apf_ctx *c) {
     if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
     free_workspace(c);
     if (c->d_eps) cudaFree(c->d_eps);
+    ridges_free(c);
     for (auto &ev : c->ev) if (ev) cudaEventDestroy(ev);
     for (auto &ev : c->prof_ev) if (ev) cudaEventDestroy(ev);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -495,9 +496,11 @@ static int finish(apf_ctx *c, cudaStream_t s, int rc_solve) {
     if (c->prof_on) prof_collect(c);
     e = cudaGetLastError();
     if (e != cudaSuccess) return check_cuda(c, e, "kernel launch");
-    int flags = 0;
-    cudaMemcpyAsync(&flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    int fl2[2] = {0, 0};
+    cudaMemcpyAsync(fl2, c->d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
+    int flags = fl2[0];
+    c->stats.leaf_fallbacks = fl2[1];
     float ms[6] = {0};
     for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]);
     c->stats.ms_boundary = ms[0];

@@ -79,7 +79,7 @@ struct apf_ctx {
     int nin = 0, nout = 0;  // channel counts used by all device-side code
     // refinement
     double ir_tol = 1e-10;
-    int ir_max = 8;
+    int ir_max = 40;
     // workspace signature
     int ws_nx = -1, ws_ny = -1, ws_h = -1, ws_min = -1, ws_mout = -1;
     long long ws_bytes = 0;
@@ -106,6 +106,12 @@ struct apf_ctx {
     int *d_flags = nullptr;
     int *d_pairs = nullptr;      // objective (b, a) pairs
     MixedWork *mw = nullptr;
+    // ridge parametrization (apf_set_ridges): edges and the slab they define
+    double *d_edges = nullptr, *d_ridge_g = nullptr;  // n_edges each
+    double *d_ridge_eps = nullptr;                     // h*nx: generated eps, then host grad_eps staging
+    int ridge_n = 0, ridge_cap = 0, ridge_h = 0, ridge_mirror = 0;
+    long long ridge_eps_cap = 0;
+    double ridge_eps_r = 0, ridge_eps_b = 0;
     // CUDA graphs (captured on cap_stream, replayed on the caller's stream)
     cudaStream_t cap_stream = nullptr;
     bool use_graphs = true;
@@ -181,3 +187,7 @@ int tc_init();
 void slab64_init_attrs();
 void mixed_init_attrs();
 int check_cuda(apf_ctx *c, cudaError_t e, const char *what);
+bool is_device_ptr(const void *p);
+
+// ridges.cu
+void ridges_free(apf_ctx *c);

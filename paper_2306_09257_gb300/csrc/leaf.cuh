@@ -565,6 +565,10 @@ constexpr int rec_smem_bytes() {
 
 static __device__ void leaf128_recursive(float *re, float *im, long long ld, int *flags) {
     extern __shared__ __align__(16) unsigned char rec_smem[];
+    // zero pivots of the recursive attempt are recorded here, not in `flags`:
+    // the self-check below catches their effect and the fallback reports
+    __shared__ int s_sing;
+    if (threadIdx.x == 0) s_sing = 0;
     float2 *M = reinterpret_cast<float2 *>(rec_smem);
     float2 *T64 = M + 128 * rec::P128, *V64 = T64 + 64 * rec::P64;
     float2 *T32 = V64 + 64 * rec::P64, *V32 = T32 + 32 * rec::P32;
@@ -579,12 +583,12 @@ static __device__ void leaf128_recursive(float *re, float *im, long long ld, int
         constexpr int H = 64;
         float2 *A = M, *B = M + H, *C = M + H * rec::P128, *D = M + H * rec::P128 + H;
         const int ld0 = rec::P128;
-        rec::inv_sym<64>(A, ld0, T32, V32, V64, flags);
+        rec::inv_sym<64>(A, ld0, T32, V32, V64, &s_sing);
         rec::gemm<H, false, false>(C, ld0, A, ld0, T64, rec::P64, 1.f);
         __syncthreads();
         rec::gemm<H, false, true>(T64, rec::P64, B, ld0, D, ld0, -1.f);
         __syncthreads();
-        rec::inv_sym<64>(D, ld0, T32, V32, V64, flags);
+        rec::inv_sym<64>(D, ld0, T32, V32, V64, &s_sing);
         rec::gemm<H, false, false>(D, ld0, T64, rec::P64, V64, rec::P64, 1.f);
         __syncthreads();
         rec::gemm<H, true, true>(T64, rec::P64, V64, rec::P64, A, ld0, 1.f);
@@ -595,6 +599,88 @@ static __device__ void leaf128_recursive(float *re, float *im, long long ld, int
             B[cc * ld0 + r] = make_float2(-v.x, -v.y);
         }
         __syncthreads();
+    }
+    // Self-check before the block is overwritten.  Pivoting stays inside the
+    // 32 x 32 leaves, so a nearly singular leading sub-block of a block that
+    // is itself well conditioned spoils the recursion; apply the computed
+    // inverse to a fixed unit-modulus probe v and compare X (X^-1 v) with v.
+    // Above 2e-5 relative residual (a sound block gives a few 1e-7) the block
+    // is inverted again by Gauss-Jordan with pivoting over all 128 rows.
+    __shared__ float2 s_y[128];
+    __shared__ float s_part[rec::NT / 32];
+    __shared__ int s_bad;
+    {
+        const int t = threadIdx.x, r = t >> 2, sub = t & 3;
+        auto probe = [](int i) {
+            float sn, cs;
+            sincosf(2.3999632f * (float)i, &sn, &cs);
+            return make_float2(cs, sn);
+        };
+        float2 y = make_float2(0.f, 0.f);
+        for (int q = 0; q < 32; ++q) {
+            const int c = sub + 4 * q;
+            const float2 m = M[r * rec::P128 + c], v = probe(c);
+            y.x += m.x * v.x - m.y * v.y;
+            y.y += m.x * v.y + m.y * v.x;
+        }
+        y.x += __shfl_xor_sync(0xffffffffu, y.x, 1);
+        y.y += __shfl_xor_sync(0xffffffffu, y.y, 1);
+        y.x += __shfl_xor_sync(0xffffffffu, y.x, 2);
+        y.y += __shfl_xor_sync(0xffffffffu, y.y, 2);
+        if (sub == 0) s_y[r] = y;
+        __syncthreads();
+        // row r of the original block, columns [32 sub, 32 sub + 32), 16-byte loads
+        float2 z = make_float2(0.f, 0.f);
+        const float *rr = re + (long long)r * ld + 32 * sub, *ri = im + (long long)r * ld + 32 * sub;
+        if (((((uintptr_t)rr) | ((uintptr_t)ri)) & 15) == 0) {
+            float4 a[8], b[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                a[q] = reinterpret_cast<const float4 *>(rr)[q];
+                b[q] = reinterpret_cast<const float4 *>(ri)[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float xr[4] = {a[q].x, a[q].y, a[q].z, a[q].w}, xi[4] = {b[q].x, b[q].y, b[q].z, b[q].w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 yc = s_y[32 * sub + 4 * q + u];
+                    z.x += xr[u] * yc.x - xi[u] * yc.y;
+                    z.y += xr[u] * yc.y + xi[u] * yc.x;
+                }
+            }
+        } else {
+            for (int q = 0; q < 32; ++q) {
+                const float xr = rr[q], xi = ri[q];
+                const float2 yc = s_y[32 * sub + q];
+                z.x += xr * yc.x - xi * yc.y;
+                z.y += xr * yc.y + xi * yc.x;
+            }
+        }
+        z.x += __shfl_xor_sync(0xffffffffu, z.x, 1);
+        z.y += __shfl_xor_sync(0xffffffffu, z.y, 1);
+        z.x += __shfl_xor_sync(0xffffffffu, z.x, 2);
+        z.y += __shfl_xor_sync(0xffffffffu, z.y, 2);
+        float e2 = 0.f;
+        if (sub == 0) {
+            const float2 v = probe(r);
+            e2 = (z.x - v.x) * (z.x - v.x) + (z.y - v.y) * (z.y - v.y);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, off);
+        if ((t & 31) == 0) s_part[t >> 5] = e2;
+        __syncthreads();
+        if (t == 0) {
+            float tot = 0.f;
+            for (int i = 0; i < rec::NT / 32; ++i) tot += s_part[i];
+            s_bad = !(tot <= 4e-10f * 128.f);  // (2e-5)^2 |v|^2; also catches NaN
+        }
+        __syncthreads();
+    }
+    if (s_bad) {
+        if (threadIdx.x == 0) atomicAdd(flags + 1, 1);  // fallback count (flags[1])
+        leaf_gj_regs<128>(re, im, ld, flags);
+        return;
     }
     for (int e = threadIdx.x; e < 128 * 128; e += rec::NT) {
         const int r = e >> 7, c = e & 127;

@@ -14,6 +14,8 @@
 #include "leaf.cuh"
 
 #include <algorithm>
+#include <stdio.h>
+#include <stdlib.h>
 #include <vector>
 
 struct MixedWork {
@@ -648,6 +650,14 @@ int mixed_alloc(apf_ctx *c) {
     mixed_free(c);
     MixedWork *w = new MixedWork();
     c->mw = w;
+    if (const char *e = getenv("APF_NSPLIT_ELIM")) {  // tuning knob: bf16 planes of the elimination (2 or 3)
+        int v = atoi(e);
+        if (v == 2 || v == 3) w->nsplit_elim = v;
+    }
+    if (const char *e = getenv("APF_LEAF_VARIANT")) {  // tuning knob: 128-block leaf kernel (0..3)
+        int v = atoi(e);
+        if (v >= 0 && v <= 3) w->leaf_variant = v;
+    }
     long long n = c->nx, h = c->h;
     int nin = c->nin, nout = c->nout;
     long long ncol = nin + nout;
@@ -724,12 +734,18 @@ static int correct_body(apf_ctx *c, cudaStream_t s) {
 
 // Float64 iterative refinement: r = R - K E, E += Khat^-1 r until
 // max_c ||r_c|| / ||R_c|| <= tol (or max_iters corrections).
+// Diagnostics: APF_IR_VERBOSE=1 prints the residual of every refinement step.
+static const bool g_ir_verbose = [] {
+    const char *e = getenv("APF_IR_VERBOSE");
+    return e && e[0] == '1';
+}();
+
 int mixed_refine(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
     int ncol = (c->nin + c->nout);
     std::vector<double> nr(ncol), ne(ncol);
-    int iters = 0, rc;
-    double ratio = 0.0;
+    int iters = 0, rc, rising = 0;
+    double ratio = 0.0, prev = INFINITY;
     for (;;) {
         if ((rc = run_graph(c, c->g_resid, s, resid_body))) return rc;
         cudaMemcpyAsync(nr.data(), w->rnorm, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
@@ -742,8 +758,13 @@ int mixed_refine(apf_ctx *c, cudaStream_t s) {
         }
         ratio = 0.0;
         for (int i = 0; i < ncol; ++i) ratio = std::max(ratio, sqrt(ne[i] / std::max(nr[i], 1e-300)));
+        if (g_ir_verbose) fprintf(stderr, "apf refinement: iteration %d, max relative residual %.3e\n", iters, ratio);
         if (!(ratio == ratio)) { ratio = INFINITY; break; }
         if (ratio <= c->ir_tol || iters >= c->ir_max) break;
+        // diverging: the residual grew on two consecutive sweeps
+        rising = ratio > prev ? rising + 1 : 0;
+        if (rising >= 2) break;
+        prev = ratio;
         if ((rc = run_graph(c, c->g_correct, s, correct_body))) return rc;
         ++iters;
     }

@@ -82,3 +82,31 @@ def test_mixed_recursive_inverse(env, n, leaf):
     ref = torch.linalg.inv(X)
     err = (torch.linalg.norm(Xi - ref) / torch.linalg.norm(ref)).item()
     assert err < 3e-4, err
+
+
+def test_leaf128_falls_back_on_singular_leading_block(env):
+    """A complex-symmetric 128 x 128 block whose leading 64 x 64 sub-block is
+    zero but which is itself well conditioned: the recursive in-CTA inversion
+    must detect its failure and recover through the fully pivoted
+    Gauss-Jordan, with no singular-pivot error."""
+    torch, apf, L = env
+    n = 128
+    g = torch.Generator(device="cpu").manual_seed(5)
+    P = torch.randn(n, n, dtype=torch.complex128, generator=g) * 0.01
+    X = torch.zeros(n, n, dtype=torch.complex128)
+    X[:64, 64:] = torch.eye(64)
+    X[64:, :64] = torch.eye(64)
+    X = X + P + P.T
+    X[:64, :64] = 0.0
+    X = X.cuda()
+    s = apf.Solver(0, "mixed")
+    s.set_grid(n, 8 + 2 * 4 + 4, 4, 4, 8.0)
+    s.set_eps(np.full((1, n), 1.5), 2.25, 1.0)
+    s.set_channels([0], [0])
+    re, im = planar(torch, X)
+    rc = L.apf_debug_inv32(s._h, n, re.data_ptr(), im.data_ptr(), 128)
+    assert rc == 0, L.apf_last_error(s._h)
+    Xi = re.double() + 1j * im.double()
+    ref = torch.linalg.inv(X)
+    err = (torch.linalg.norm(Xi - ref) / torch.linalg.norm(ref)).item()
+    assert err < 3e-4, err
