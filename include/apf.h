@@ -135,6 +135,34 @@ int apf_solve_S_grad(apf_ctx *ctx, int objective, const double *params, int n_pa
    solve (Eq. 1 with Eq. 3).  grad_eps: h*nx float64. */
 int apf_grad_from_gamma(apf_ctx *ctx, const double *Gamma, double *grad_eps, void *stream);
 
+/* Orders propagating in the substrate (the reflection channels): *n gets the
+   count, m (host, may be NULL) the orders, ascending.  Requires set_grid and
+   set_eps. */
+int apf_substrate_orders(const apf_ctx *ctx, int *n, int *m);
+
+/* Reflection block of the last solve (paper Sec. 2: S = C A^-1 B - D, with D
+   the identity on the reflected channels; Supplement Sec. 1 takes B and C
+   from both sides of the structure).  R[b][a] = sqrt(nu_b) u_{m_b}^H E_a on
+   the source row minus [m_b == m_a] (the incident wave), for input a and
+   substrate order m_ref[b] (host ints, each propagating in the substrate;
+   NULL or n_ref = 0: all of apf_substrate_orders).  R: n_ref x n_in
+   complex128, [b][a], host or device.  The field on the source row comes
+   from the first slab row by the back substitution of the substrate rows,
+   per Fourier order.  With lossless permittivity, sum_b |S_ba|^2 over all
+   cladding orders plus sum_b |R_ba|^2 over all substrate orders is 1 up to
+   the PML reflection (flux conservation).  Enqueues on `stream` and
+   synchronizes it. */
+int apf_reflection(apf_ctx *ctx, const int *m_ref, int n_ref, double *R, void *stream);
+
+/* Transmission from the cladding side, from the adjoint fields of the last
+   solve (A = A^T: the adjoint column of output b is the field of a cladding
+   source of order -m_b, scaled by i/2).  S_rev[p][q]: from cladding order
+   m_out[q] into substrate order m_in[p], n_in x n_out complex128, [p][q],
+   host or device; needs -m in the output set for every output order m
+   (APF_EINVAL otherwise; the default channel set qualifies).  Reciprocity
+   (paper Sec. 2, dA/dp symmetric) makes S_rev[p(-m_a)][q(-m_b)] = S[b][a]. */
+int apf_reverse_S(apf_ctx *ctx, double *S_rev, void *stream);
+
 /* Ridge metasurface parametrization (paper Sec. 3 and Eq. 5: the design
    variables are the edge positions of the ridges; mirror symmetry maps the
    free half period onto the other half, Supplement Sec. 6 frees all edges).

@@ -29,6 +29,7 @@ EXPORTS = ("apf_create", "apf_destroy", "apf_set_grid", "apf_set_eps", "apf_set_
            "apf_get_channels", "apf_solve_S", "apf_solve_S_grad", "apf_grad_from_gamma",
            "apf_set_refinement", "apf_get_stats", "apf_set_profiling", "apf_get_profile",
            "apf_solve_S_noalloc", "apf_last_error", "apf_version", "apf_set_ridges", "apf_ridge_grad",
+           "apf_substrate_orders", "apf_reflection", "apf_reverse_S",
            "apf_sno_create", "apf_sno_destroy", "apf_sno_num_params", "apf_sno_set_params",
            "apf_sno_get_params", "apf_sno_forward", "apf_sno_gradients", "apf_sno_train_step")
 
@@ -90,6 +91,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.apf_set_profiling.argtypes = [vp, i]
     L.apf_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
     L.apf_solve_S_noalloc.argtypes = [i, i, i, i, d, ctypes.POINTER(PML), dp, i, i, d, d, ip, i, ip, i, dp, vp]
+    L.apf_substrate_orders.argtypes = [vp, ip, ip]
+    L.apf_reflection.argtypes = [vp, ip, i, dp, vp]
+    L.apf_reverse_S.argtypes = [vp, dp, vp]
     L.apf_set_ridges.argtypes = [vp, dp, i, i, d, d, i, i, d, d, dp]
     L.apf_ridge_grad.argtypes = [vp, dp, dp, vp]
     L.apf_last_error.argtypes = [vp]
@@ -213,6 +217,36 @@ class Solver:
         mo = (ctypes.c_int * no.value)()
         self._check(self._L.apf_get_channels(self._h, None, None, mi, mo))
         return np.array(mi[:], dtype=np.int64), np.array(mo[:], dtype=np.int64)
+
+    def substrate_orders(self) -> np.ndarray:
+        """Orders propagating in the substrate (the reflection channels)."""
+        n = ctypes.c_int()
+        self._check(self._L.apf_substrate_orders(self._h, ctypes.byref(n), None))
+        m = (ctypes.c_int * n.value)()
+        self._check(self._L.apf_substrate_orders(self._h, None, m))
+        return np.array(m[:], dtype=np.int64)
+
+    def reflection(self, m_ref: Optional[Sequence[int]] = None, out=None):
+        """Reflection block of the last solve (see apf_reflection): rows =
+        substrate orders m_ref (default: all of substrate_orders()), columns =
+        inputs."""
+        mr = self.substrate_orders() if m_ref is None else np.asarray(m_ref)
+        mi, _ = self.channels()
+        R = np.empty((len(mr), len(mi)), dtype=np.complex128) if out is None else out
+        arr = (ctypes.c_int * len(mr))(*[int(v) for v in mr])
+        st = _stream_of(R)
+        self._check(self._L.apf_reflection(self._h, arr, len(mr), _ptr(R, np.complex128), st))
+        return R
+
+    def reverse_S(self, out=None):
+        """Transmission from the cladding side of the last solve (see
+        apf_reverse_S): rows = substrate orders m_in, columns = cladding
+        orders m_out."""
+        mi, mo = self.channels()
+        S = np.empty((len(mi), len(mo)), dtype=np.complex128) if out is None else out
+        st = _stream_of(S)
+        self._check(self._L.apf_reverse_S(self._h, _ptr(S, np.complex128), st))
+        return S
 
     def set_refinement(self, tol: float, max_iters: int):
         self._check(self._L.apf_set_refinement(self._h, float(tol), int(max_iters)))

@@ -67,6 +67,8 @@ static void free_workspace(apf_ctx *c) {
     c->d_S = c->d_Gam = c->d_Q = c->d_fft = nullptr;
     c->d_grad = c->d_f = c->d_colnorm = nullptr;
     c->d_flags = nullptr; c->d_pairs = nullptr;
+    c->d_qsrc = c->d_refl = c->d_srev = nullptr;
+    c->d_mref = c->d_rmap = nullptr;
 }
 
 template <typename T>
@@ -104,6 +106,8 @@ static int ensure_workspace(apf_ctx *c) {
     AL(c->d_S, (long long)nout * nin); AL(c->d_Gam, (long long)nout * nin);
     AL(c->d_Q, h * nout * nx); AL(c->d_grad, h * nx);
     AL(c->d_f, 8); AL(c->d_colnorm, 2 * ncol); AL(c->d_flags, 4);
+    AL(c->d_qsrc, nx); AL(c->d_refl, nx * nin); AL(c->d_srev, (long long)nin * nout);
+    AL(c->d_mref, nx); AL(c->d_rmap, nout);
 #undef AL
     if (c->precision != APF_FP64) {
         if ((rc = mixed_alloc(c)) != APF_OK) { free_workspace(c); return rc; }
@@ -583,6 +587,85 @@ int apf_grad_from_gamma(apf_ctx *c, const double *Gamma, double *grad_eps, void 
     float ms = 0;
     cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
     c->stats.ms_gradient = ms;
+    return APF_OK;
+}
+
+
+int apf_substrate_orders(const apf_ctx *c, int *n, int *m) {
+    if (!c) return APF_EINVAL;
+    if (!c->grid_set || !c->eps_set) return APF_ESTATE;
+    int cnt = 0;
+    for (int o = -(c->nx / 2); o < c->nx - c->nx / 2; ++o) {
+        double q = disp_q(c, o, c->eps_sub);
+        if (q > 0.0 && q < 1.0) {
+            if (m) m[cnt] = o;
+            ++cnt;
+        }
+    }
+    if (n) *n = cnt;
+    return APF_OK;
+}
+
+int apf_reflection(apf_ctx *c, const int *m_ref, int n_ref, double *R, void *stream) {
+    if (!c) return APF_EINVAL;
+    if (!R) return set_err(c, APF_EINVAL, "R is NULL");
+    if (!c->ch_set || c->ws_nx < 0) return set_err(c, APF_ESTATE, "apf_reflection needs a previous solve");
+    std::vector<int> ord;
+    if (m_ref && n_ref > 0) {
+        if (n_ref > c->nx) return set_err(c, APF_EINVAL, "n_ref=%d exceeds nx=%d", n_ref, c->nx);
+        ord.assign(m_ref, m_ref + n_ref);
+        for (int o : ord) {
+            double q = disp_q(c, o, c->eps_sub);
+            if (!(q > 0.0 && q < 1.0))
+                return set_err(c, APF_EINVAL, "reflection order %d does not propagate in the substrate", o);
+        }
+    } else {
+        for (int o = -(c->nx / 2); o < c->nx - c->nx / 2; ++o) {
+            double q = disp_q(c, o, c->eps_sub);
+            if (q > 0.0 && q < 1.0) ord.push_back(o);
+        }
+    }
+    const int nr = (int)ord.size();
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(c->d_mref, ord.data(), sizeof(int) * nr, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return check_cuda(c, e, "upload reflection orders");
+    launch_source_row(c, c->d_qsrc, s);
+    // first slab row of the forward columns, to the Fourier basis
+    launch_fft(c, c->d_E, c->d_fft, c->nx, c->nin, c->nx, c->nx, -1, 1.0 / sqrt((double)c->nx), s);
+    launch_reflection(c, c->d_fft, c->d_qsrc, c->d_mref, nr, c->d_refl, s);
+    e = cudaMemcpyAsync(R, c->d_refl, sizeof(double2) * (size_t)nr * c->nin, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return check_cuda(c, e, "reflection");
+    return APF_OK;
+}
+
+int apf_reverse_S(apf_ctx *c, double *S_rev, void *stream) {
+    if (!c) return APF_EINVAL;
+    if (!S_rev) return set_err(c, APF_EINVAL, "S_rev is NULL");
+    if (!c->ch_set || c->ws_nx < 0) return set_err(c, APF_ESTATE, "apf_reverse_S needs a previous solve");
+    std::vector<int> rmap(c->nout);
+    for (int q = 0; q < c->nout; ++q) {
+        int hit = -1;
+        for (int b = 0; b < c->nout; ++b)
+            if (c->m_out[b] == -c->m_out[q]) { hit = b; break; }
+        if (hit < 0)
+            return set_err(c, APF_EINVAL, "reverse transmission needs order %d in the output set (output %d)",
+                           -c->m_out[q], c->m_out[q]);
+        rmap[q] = hit;
+    }
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ncol = c->nin + c->nout;
+    cudaError_t e = cudaMemcpyAsync(c->d_rmap, rmap.data(), sizeof(int) * c->nout, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return check_cuda(c, e, "upload order map");
+    launch_fft(c, c->d_E, c->d_fft, c->nx, ncol, c->nx, c->nx, -1, 1.0 / sqrt((double)c->nx), s);
+    launch_reverse_S(c, c->d_fft, c->d_rmap, c->d_srev, s);
+    e = cudaMemcpyAsync(S_rev, c->d_srev, sizeof(double2) * (size_t)c->nin * c->nout, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return check_cuda(c, e, "reverse S");
     return APF_OK;
 }
 

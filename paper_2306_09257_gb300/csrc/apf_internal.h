@@ -98,6 +98,11 @@ struct apf_ctx {
     double2 *d_T = nullptr;      // ncol*nx temp
     double2 *d_R = nullptr;      // h*ncol*nx residual (mixed)
     double2 *d_S = nullptr, *d_Gam = nullptr;  // n_out*n_in
+    double2 *d_qsrc = nullptr;   // nx: source-row coefficient q[m] of the substrate side
+    double2 *d_refl = nullptr;   // nx*n_in: reflection block (apf_reflection)
+    double2 *d_srev = nullptr;   // n_in*n_out: transmission from the cladding side (apf_reverse_S)
+    int *d_mref = nullptr;       // nx: reflection orders
+    int *d_rmap = nullptr;       // n_out: adjoint column of the opposite output order
     double2 *d_Q = nullptr;      // h*n_out*nx
     double2 *d_fft = nullptr;    // ncol*nx
     double *d_grad = nullptr;    // h*nx
@@ -145,6 +150,10 @@ GridDev make_grid(const apf_ctx *c);
 // boundary.cu
 void launch_boundary(apf_ctx *c, cudaStream_t s);
 void launch_build_rhs(apf_ctx *c, double2 *E, cudaStream_t s);
+void launch_source_row(apf_ctx *c, double2 *q, cudaStream_t s);
+void launch_reflection(apf_ctx *c, const double2 *fft0, const double2 *q, const int *m_ref, int n_ref, double2 *R,
+                       cudaStream_t s);
+void launch_reverse_S(apf_ctx *c, const double2 *fft0, const int *rmap, double2 *Srev, cudaStream_t s);
 void launch_twiddles(apf_ctx *c, cudaStream_t s);
 void launch_fft(apf_ctx *c, const double2 *in, double2 *out, int n, int batch, long long in_stride,
                 long long out_stride, int sign, double scale, cudaStream_t s);

@@ -171,7 +171,87 @@ __global__ void k_fft(const double2 *in, double2 *out, int n, int logn, long lon
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = cscale(a[i], scale);
 }
 
+// Source-row map of the substrate side, per Fourier order m: with the rows
+// below the slab eliminated upward (pivots dt_j, couplings c_j = 1/s_{j-1/2}),
+// back substitution gives the field on the source row as
+//   u_src = fac[m] u_{j0} + q[m] b,
+// u_{j0} the first slab row, b the source coefficient on the source row;
+// fac is the boundary sweep's product of c_{i+1}/dt_i over i = src..j0-1 (A
+// is symmetric, so the same factor carries the source up), and
+// q = sum_{j=src}^{j0-1} G_j^2 / dt_j with G_src = 1, G_{j+1} = G_j c_{j+1}/dt_j.
+__global__ void k_source_row(GridDev g, const double2 *st, double2 *q) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= g.nx) return;
+    const double2 *ish = st + g.ny + 1;
+    double sp = sinpi((double)m / (double)g.nx);
+    double lam = 4.0 * sp * sp;
+    double2 dt = row_diag(g, st, 0, lam, g.eps_sub);
+    double2 G = cmk(1.0, 0.0), acc = cmk(0.0, 0.0);
+    for (int j = 0; j < g.j0; ++j) {
+        if (j > 0) dt = csub(row_diag(g, st, j, lam, g.eps_sub), cmul(cmul(ish[j], ish[j]), cinv(dt)));
+        if (j >= g.jsrc) {
+            const double2 idt = cinv(dt);
+            acc = cadd(acc, cmul(cmul(G, G), idt));
+            G = cmul(G, cmul(ish[j + 1], idt));
+        }
+    }
+    q[m] = acc;
+}
+
+// Reflection block: R[b][a] = sqrt(nu_b) (fac[m_b] ehat_a[m_b] + [m_b == m_a] q[m_a] beta_a)
+// - [m_b == m_a], beta_a = -2i sqrt(nu_a) the source coefficient of input a, ehat
+// the (1/sqrt(nx)) FFT of forward column a on the first slab row.
+__global__ void k_reflection(GridDev g, const double2 *fft0, const double2 *modes, const double2 *q,
+                             const int *m_in, int n_in, const int *m_ref, int n_ref, double2 *R) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    int b = blockIdx.y;
+    if (a >= n_in || b >= n_ref) return;
+    const int mb = m_ref[b], ib = mod_nx(mb, g.nx);
+    const double nub = nu_of(g, mb, g.eps_sub);
+    double2 u = cmul(modes[2 * g.nx + ib], fft0[(long long)a * g.nx + ib]);
+    const bool diag = (mb == m_in[a]);
+    if (diag) u = cadd(u, cmul(q[ib], cmk(0.0, -2.0 * sqrt(nub))));
+    double2 r = cscale(u, sqrt(nub));
+    if (diag) r.x -= 1.0;
+    R[(long long)b * n_in + a] = r;
+}
+
+// Transmission from the cladding side: adjoint column b solved A Phi_b = C_b^T,
+// and a cladding source of order -m_b is -2i C_b^T, so the field it makes on
+// the first slab row is -2i Phi_b.  Srev[p][qq] = sqrt(nu_p) fac[m_p] (-2i)
+// phihat_{b}[m_p] with m_p = m_in[p] (substrate order) and b = rmap[qq] the
+// adjoint column with m_out[b] = -m_out[qq] (cladding order m_out[qq]).
+__global__ void k_reverse_S(GridDev g, const double2 *fft0, const double2 *modes, const int *m_in, int n_in,
+                            const int *rmap, int n_out, double2 *Srev) {
+    int qq = blockIdx.x * blockDim.x + threadIdx.x;
+    int p = blockIdx.y;
+    if (qq >= n_out || p >= n_in) return;
+    const int mp = m_in[p], ip = mod_nx(mp, g.nx);
+    const double nup = nu_of(g, mp, g.eps_sub);
+    const double2 phi = fft0[(long long)(n_in + rmap[qq]) * g.nx + ip];
+    const double2 u = cmul(cmul(modes[2 * g.nx + ip], phi), cmk(0.0, -2.0));
+    Srev[(long long)p * n_out + qq] = cscale(u, sqrt(nup));
+}
+
 }  // namespace
+
+void launch_source_row(apf_ctx *c, double2 *q, cudaStream_t s) {
+    GridDev g = make_grid(c);
+    APF_LAUNCH(c, k_source_row, (c->nx + 127) / 128, 128, 0, s, g, c->d_stretch, q);
+}
+
+void launch_reflection(apf_ctx *c, const double2 *fft0, const double2 *q, const int *m_ref, int n_ref, double2 *R,
+                       cudaStream_t s) {
+    GridDev g = make_grid(c);
+    dim3 grid((c->nin + 127) / 128, n_ref);
+    APF_LAUNCH(c, k_reflection, grid, 128, 0, s, g, fft0, c->d_modes, q, c->d_min, c->nin, m_ref, n_ref, R);
+}
+
+void launch_reverse_S(apf_ctx *c, const double2 *fft0, const int *rmap, double2 *Srev, cudaStream_t s) {
+    GridDev g = make_grid(c);
+    dim3 grid((c->nout + 127) / 128, c->nin);
+    APF_LAUNCH(c, k_reverse_S, grid, 128, 0, s, g, fft0, c->d_modes, c->d_min, c->nin, rmap, c->nout, Srev);
+}
 
 int fft_smem_bytes(int n) { return n * (int)sizeof(double2); }
 
