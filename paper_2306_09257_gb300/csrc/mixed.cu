@@ -128,6 +128,69 @@ __global__ void __launch_bounds__(256) k_pack32(PackJobs jobs) {
     }
 }
 
+// Vectorised form of k_pack32 for whole 32 x 64 tiles (R % 32 == 0, K % 64 == 0,
+// ld % 4 == 0, 16-byte aligned planes): 128-bit loads into shared memory, then
+// each thread splits 8 consecutive k of one row and writes 16-byte rows of
+// every plane.
+__device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (*v)[3], int p, bool neg) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat16 lo = v[2 * i][p], hi = v[2 * i + 1][p];
+        if (neg) { lo = __hneg(lo); hi = __hneg(hi); }
+        w[i] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__global__ void __launch_bounds__(256) k_pack32v(PackJobs jobs) {
+    const PackJob &J = jobs.j[blockIdx.z];
+    __shared__ float tre[32][65], tim[32][65];
+    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+    if (r0 >= J.R || k0 >= J.K) return;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int idx = t + 256 * h;
+        if (!J.trans) {
+            const int row = idx >> 4, c4 = idx & 15;
+            const long long g = (long long)(r0 + row) * J.ld + k0 + 4 * c4;
+            const float4 a = *reinterpret_cast<const float4 *>(J.re + g), b = *reinterpret_cast<const float4 *>(J.im + g);
+            tre[row][4 * c4] = a.x; tre[row][4 * c4 + 1] = a.y; tre[row][4 * c4 + 2] = a.z; tre[row][4 * c4 + 3] = a.w;
+            tim[row][4 * c4] = b.x; tim[row][4 * c4 + 1] = b.y; tim[row][4 * c4 + 2] = b.z; tim[row][4 * c4 + 3] = b.w;
+        } else {
+            const int krow = idx >> 3, c4 = idx & 7;
+            const long long g = (long long)(k0 + krow) * J.ld + r0 + 4 * c4;
+            const float4 a = *reinterpret_cast<const float4 *>(J.re + g), b = *reinterpret_cast<const float4 *>(J.im + g);
+            tre[4 * c4][krow] = a.x; tre[4 * c4 + 1][krow] = a.y; tre[4 * c4 + 2][krow] = a.z; tre[4 * c4 + 3][krow] = a.w;
+            tim[4 * c4][krow] = b.x; tim[4 * c4 + 1][krow] = b.y; tim[4 * c4 + 2][krow] = b.z; tim[4 * c4 + 3][krow] = b.w;
+        }
+    }
+    __syncthreads();
+    const int r = t >> 3, c = t & 7;
+    const int row = r0 + r, k = k0 + 8 * c;
+    __nv_bfloat16 sr[8][3], si[8][3];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        split_bf16(tre[r][8 * c + u], J.nsplit, sr[u]);
+        split_bf16(tim[r][8 * c + u], J.nsplit, si[u]);
+    }
+    const long long kp = J.kp, K = J.K, R = J.R;
+    for (int p = 0; p < J.nsplit; ++p) {
+        __nv_bfloat16 *o = J.out + p * J.plane_pitch;
+        const uint4 re = pack8(sr, p, false), im = pack8(si, p, false);
+        if (!J.layoutB) {
+            *reinterpret_cast<uint4 *>(o + row * kp + k) = re;
+            *reinterpret_cast<uint4 *>(o + row * kp + K + k) = im;
+        } else {
+            *reinterpret_cast<uint4 *>(o + row * kp + k) = re;
+            *reinterpret_cast<uint4 *>(o + row * kp + K + k) = pack8(si, p, true);
+            *reinterpret_cast<uint4 *>(o + (R + row) * kp + k) = im;
+            *reinterpret_cast<uint4 *>(o + (R + row) * kp + K + k) = re;
+        }
+    }
+}
+
 // A-layout pack of complex float64 rows (optionally the sum of two sources):
 // row r = [Re v(r,:), Im v(r,:)], v = s1 (+ s2).
 __global__ void k_pack64_A(const double2 *__restrict__ s1, const double2 *__restrict__ s2, long long ld, int R,
@@ -180,24 +243,39 @@ __global__ void k_pack64_BT(const double2 *__restrict__ src, long long ld, int R
 
 // X_j = K_j - G_{j-1} in float32 planes (K_j: 5-point slab block plus the
 // boundary circulants on the first / last slab row).
+// X_j = K_j - G_{j-1} in float32 planes (K_j: 4 - k^2 eps on the diagonal,
+// -1 on the periodic neighbours, the circulants Sigma_bot / Sigma_top on the
+// first / last slab row).  Thread: 4 consecutive columns xp of row x (n % 4 == 0).
 __global__ void k_assemble32(GridDev g, int row, const double *eps, const double2 *circ, const float *Gre,
                              const float *Gim, float *Xre, float *Xim) {
     const int n = g.nx;
     const int x = blockIdx.y;
-    const int xp = blockIdx.x * blockDim.x + threadIdx.x;
-    if (xp >= n) return;
-    float vr = 0.f, vi = 0.f;
-    if (xp == x) vr = (float)(4.0 - g.k * g.k * eps[(long long)row * n + x]);
-    const int dx = x - xp;
-    if (dx == 1 || dx == -1 || dx == n - 1 || dx == 1 - n) vr -= 1.f;
-    if (n == 2 && dx != 0) vr -= 1.f;  // both periodic neighbours coincide
-    const int d = dx < 0 ? dx + n : dx;
-    if (row == 0) { vr += (float)circ[d].x; vi += (float)circ[d].y; }
-    if (row == g.h - 1) { vr += (float)circ[n + d].x; vi += (float)circ[n + d].y; }
-    const long long idx = (long long)x * n + xp;
-    if (Gre) { vr -= Gre[idx]; vi -= Gim[idx]; }
-    Xre[idx] = vr;
-    Xim[idx] = vi;
+    const int xp0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (xp0 >= n) return;
+    const long long idx = (long long)x * n + xp0;
+    float vr[4] = {0.f, 0.f, 0.f, 0.f}, vi[4] = {0.f, 0.f, 0.f, 0.f};
+    if (Gre) {
+        const float4 a = *reinterpret_cast<const float4 *>(Gre + idx), b = *reinterpret_cast<const float4 *>(Gim + idx);
+        vr[0] = -a.x; vr[1] = -a.y; vr[2] = -a.z; vr[3] = -a.w;
+        vi[0] = -b.x; vi[1] = -b.y; vi[2] = -b.z; vi[3] = -b.w;
+    }
+    const float diag = (float)(4.0 - g.k * g.k * eps[(long long)row * n + x]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int xp = xp0 + u;
+        float kr = 0.f, ki = 0.f;
+        if (xp == x) kr = diag;
+        const int dx = x - xp;
+        if (dx == 1 || dx == -1 || dx == n - 1 || dx == 1 - n) kr -= 1.f;
+        if (n == 2 && dx != 0) kr -= 1.f;  // both periodic neighbours coincide
+        const int d = dx < 0 ? dx + n : dx;
+        if (row == 0) { kr += (float)circ[d].x; ki += (float)circ[d].y; }
+        if (row == g.h - 1) { kr += (float)circ[n + d].x; ki += (float)circ[n + d].y; }
+        vr[u] += kr;
+        vi[u] += ki;
+    }
+    *reinterpret_cast<float4 *>(Xre + idx) = make_float4(vr[0], vr[1], vr[2], vr[3]);
+    *reinterpret_cast<float4 *>(Xim + idx) = make_float4(vi[0], vi[1], vi[2], vi[3]);
 }
 
 // Float32 Gauss-Jordan inverse of an n x n (n <= 128) diagonal block with
@@ -430,18 +508,32 @@ __global__ void k_axpy(double2 *E, const double2 *d, long long n) {
     if (i < n) E[i] = cadd(E[i], d[i]);
 }
 
-__global__ void k_grad_rowdot32(const double2 *E, const float *Qre, const float *Qim, int j, int nx, int n_in,
-                                int n_out, double k2, double *g) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= nx) return;
-    int ncol = n_in + n_out;
-    const double2 *phi = E + ((long long)j * ncol + n_in) * nx + x;
+// g_j(x) = 2 k^2 Re sum_b Phi_j[b][x] Q[b][x].  Block: 32 consecutive x (lanes)
+// x 8 warps, warp w summing b = w, w + 8, ...; the 8 partial sums are added in
+// a fixed order (deterministic).
+__global__ void __launch_bounds__(256) k_grad_rowdot32(const double2 *E, const float *Qre, const float *Qim, int j,
+                                                       int nx, int n_in, int n_out, double k2, double *g) {
+    __shared__ double part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = blockIdx.x * 32 + lane;
+    const int ncol = n_in + n_out;
     double acc = 0.0;
-    for (int b = 0; b < n_out; ++b) {
-        double2 p = phi[(long long)b * nx];
-        acc += p.x * (double)Qre[(long long)b * nx + x] - p.y * (double)Qim[(long long)b * nx + x];
+    if (x < nx) {
+        const double2 *phi = E + ((long long)j * ncol + n_in) * nx + x;
+        for (int b = w; b < n_out; b += 8) {
+            const double2 p = phi[(long long)b * nx];
+            acc = fma(p.x, (double)Qre[(long long)b * nx + x], acc);
+            acc = fma(-p.y, (double)Qim[(long long)b * nx + x], acc);
+        }
     }
-    g[(long long)j * nx + x] = 2.0 * k2 * acc;
+    part[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && x < nx) {
+        double t = part[0][lane];
+#pragma unroll
+        for (int i = 1; i < 8; ++i) t += part[i][lane];
+        g[(long long)j * nx + x] = 2.0 * k2 * t;
+    }
 }
 
 long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
@@ -487,7 +579,15 @@ void launch_jobs(apf_ctx *c, const PackJob *js, int nj, cudaStream_t s) {
         maxK = std::max(maxK, js[i].K);
     }
     dim3 grid((maxK + 63) / 64, (maxR + 31) / 32, nj);
-    APF_LAUNCH(c, k_pack32, grid, dim3(32, 8), 0, s, jobs);
+    bool vec = true;
+    for (int i = 0; i < nj; ++i) {
+        const PackJob &J = js[i];
+        vec = vec && J.R % 32 == 0 && J.K % 64 == 0 && J.ld % 4 == 0 && J.R == maxR && J.K == maxK &&
+              ((((uintptr_t)J.re) | ((uintptr_t)J.im) | ((uintptr_t)J.out)) & 15) == 0 && J.kp % 8 == 0 &&
+              J.plane_pitch % 8 == 0;
+    }
+    if (vec) APF_LAUNCH(c, k_pack32v, grid, 256, 0, s, jobs);
+    else APF_LAUNCH(c, k_pack32, grid, dim3(32, 8), 0, s, jobs);
 }
 
 PackView pack32(apf_ctx *c, __nv_bfloat16 *dst, const PV &src, int R, int K, bool trans, bool layoutB, int nsplit,
@@ -688,7 +788,7 @@ int mixed_eliminate(apf_ctx *c, cudaStream_t s) {
     if (!w) return set_err(c, APF_ESTATE, "mixed workspace missing");
     GridDev g = make_grid(c);
     int n = c->nx;
-    dim3 agrid((n + 255) / 256, n);
+    dim3 agrid((n / 4 + 255) / 256, n);
     PV X{w->Xre, w->Xim, n};
     APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, 0, c->d_eps, c->d_circ, (const float *)nullptr,
                (const float *)nullptr, w->Xre, w->Xim);
@@ -786,7 +886,7 @@ int mixed_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s) {
         PackView pb = pack64BT(c, w->PB, c->d_E + j * L, nx, nx, nin, ns, s);
         int rc = tc_gemm(c, pa, pb, ns, nout, 2 * nx, nx, 1.f, 0.f, Qre, Qim, nx, nullptr, nullptr, 0, s);
         if (rc) return rc;
-        APF_LAUNCH(c, k_grad_rowdot32, (nx + 255) / 256, 256, 0, s, c->d_E, Qre, Qim, j, nx, nin, nout, c->k * c->k,
+        APF_LAUNCH(c, k_grad_rowdot32, (nx + 31) / 32, 256, 0, s, c->d_E, Qre, Qim, j, nx, nin, nout, c->k * c->k,
                    c->d_grad);
     }
     return APF_OK;
