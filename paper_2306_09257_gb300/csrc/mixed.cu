@@ -259,12 +259,12 @@ __global__ void k_assemble32(GridDev g, int row, const double *eps, const double
         vr[0] = -a.x; vr[1] = -a.y; vr[2] = -a.z; vr[3] = -a.w;
         vi[0] = -b.x; vi[1] = -b.y; vi[2] = -b.z; vi[3] = -b.w;
     }
-    const float diag = (float)(4.0 - g.k * g.k * eps[(long long)row * n + x]);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int xp = xp0 + u;
         float kr = 0.f, ki = 0.f;
-        if (xp == x) kr = diag;
+        // float64 only on the one diagonal element (the FP64 pipe is narrow)
+        if (xp == x) kr = (float)(4.0 - g.k * g.k * eps[(long long)row * n + x]);
         const int dx = x - xp;
         if (dx == 1 || dx == -1 || dx == n - 1 || dx == 1 - n) kr -= 1.f;
         if (n == 2 && dx != 0) kr -= 1.f;  // both periodic neighbours coincide
@@ -913,6 +913,7 @@ extern "C" int apf_debug_cgemm(apf_ctx *c, int m, int n, int k, const float *Are
     PackView B = pack32(c, pb, PV{(float *)Bre, (float *)Bim, n}, n, k, true, true, nsplit, s);
     int rc = tc_gemm(c, A, B, nsplit, m, 2 * n, n, 1.f, 0.f, Cre, Cim, n, nullptr, nullptr, 0, s);
     cudaError_t e = cudaDeviceSynchronize();
+    if (c->prof_on) prof_collect(c);  // GEMM event timings of this call
     int fl = 0;
     cudaMemcpy(&fl, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost);
     if (tmpflags) { cudaFree(tmpflags); c->d_flags = nullptr; }
