@@ -366,14 +366,13 @@ __device__ void leaf_gj_regs2(float *re, float *im, long long ld, int *flags) {
 // The block stays in shared memory; the 2x2 Schur recursion of the global
 // inversion (T = C Ai, D -= T B, D <- D^-1, V = D T, A += T^T V, C = -V,
 // B = -V^T) runs down to 32 x 32 diagonal blocks, which are inverted by
-// pivoted Gauss-Jordan on 4 warps with the rows in registers.  The products
+// pivoted Gauss-Jordan on 8 warps with the rows in registers.  The products
 // are CTA-wide fp32 GEMMs from shared memory.  512 threads, one CTA per block.
 // ---------------------------------------------------------------------------
 namespace rec {
 constexpr int NT = 512;
 constexpr int P128 = 130, P64 = 66, P32 = 34;  // padded pitches (float2)
 
-__device__ __forceinline__ void bar4() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // C = (ACC ? C : 0) + sgn * op(A) B, all H x H (H = 32 or 64), in shared memory
 // (every block offset and pitch even, so column pairs are 16-byte aligned).
@@ -441,39 +440,48 @@ __device__ void gemm(const float2 *A, int lda, const float2 *B, int ldb, float2 
         }
 }
 
-// Pivoted Gauss-Jordan inverse of a 32 x 32 block (pitch ld) by warps 0..3:
-// lane i holds row i, warp w the columns 8w..8w+7, in registers.  Pivot rows
-// are not swapped: step k takes the unused row p_k with the largest
-// |a[p][k]| and eliminates column k from every other row, so that at the end
-// storage row r holds row ipiv[r] of the inverse with its columns in pivot
-// order: inv[ipiv[r]][p_c] = a[r][c].
+// Pivoted Gauss-Jordan inverse of a 32 x 32 block (pitch ld) by NW warps
+// (8 by default): lane i holds row i, warp w the columns CW w .. CW w + CW - 1
+// (CW = 32 / NW), in registers.  Pivot rows are not swapped: step k takes the
+// unused row p_k with the largest |a[p][k]| and eliminates column k from every
+// other row, so that at the end storage row r holds row ipiv[r] of the inverse
+// with its columns in pivot order: inv[ipiv[r]][p_c] = a[r][c].
 // After each step every warp also stores its columns to a copy in shared
 // memory (two copies, alternating by step), and the warp owning the next
 // pivot column picks the pivot with one warp max-reduction over the key
 // (|a[i][k]|^2 with its five low mantissa bits replaced by 31 - i, so ties go
-// to the lowest row); after the step's one 128-thread barrier each warp reads
-// the pivot row and column from the copy.  `scr` holds 2 x 32 x LEAF_SP
+// to the lowest row); after the step's one barrier of the NW warps each warp
+// reads the pivot row and column from the copy.  `scr` holds 2 x 32 x LEAF_SP
 // float2, 16-byte aligned.
 constexpr int LEAF_SP = 34;
 
-static __device__ void leaf32(float2 *a, int ld, float2 *scr, int *flags) {
+template <int NW>
+static __device__ void leaf32t(float2 *a, int ld, float2 *scr, int *flags) {
+    constexpr int CW = 32 / NW;  // columns per warp
     __shared__ int pp[2], piv[32];
-    if (threadIdx.x >= 128) return;
+    if (threadIdx.x >= 32 * NW) return;
+    auto bar = [] { asm volatile("bar.sync 1, %0;" ::"n"(32 * NW) : "memory"); };
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float2 x[8];
+    float2 x[CW];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = a[lane * ld + 8 * w + j];
+    for (int j = 0; j < CW; ++j) x[j] = a[lane * ld + CW * w + j];
     // store this warp's columns to copy `b`; the owner of column k picks its pivot
     auto stage = [&](int b, int k, bool used) {
-        float4 *dst = reinterpret_cast<float4 *>(scr + (b * 32 + lane) * LEAF_SP + 8 * w);
+        float4 *dst = reinterpret_cast<float4 *>(scr + (b * 32 + lane) * LEAF_SP + CW * w);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) dst[j] = make_float4(x[2 * j].x, x[2 * j].y, x[2 * j + 1].x, x[2 * j + 1].y);
-        if (w == (k >> 3)) {
-            const int kl = k & 7;
-            const float2 s0 = (kl & 1) ? x[1] : x[0], s1 = (kl & 1) ? x[3] : x[2];
-            const float2 s2 = (kl & 1) ? x[5] : x[4], s3 = (kl & 1) ? x[7] : x[6];
-            const float2 t0 = (kl & 2) ? s1 : s0, t1 = (kl & 2) ? s3 : s2;
-            const float2 fk = (kl & 4) ? t1 : t0;
+        for (int j = 0; j < CW / 2; ++j) dst[j] = make_float4(x[2 * j].x, x[2 * j].y, x[2 * j + 1].x, x[2 * j + 1].y);
+        if (w == k / CW) {
+            const int kl = k % CW;
+            float2 fk;
+            if constexpr (CW == 8) {
+                const float2 s0 = (kl & 1) ? x[1] : x[0], s1 = (kl & 1) ? x[3] : x[2];
+                const float2 s2 = (kl & 1) ? x[5] : x[4], s3 = (kl & 1) ? x[7] : x[6];
+                const float2 t0 = (kl & 2) ? s1 : s0, t1 = (kl & 2) ? s3 : s2;
+                fk = (kl & 4) ? t1 : t0;
+            } else {
+                const float2 s0 = (kl & 1) ? x[1] : x[0], s1 = (kl & 1) ? x[3] : x[2];
+                fk = (kl & 2) ? s1 : s0;
+            }
             const unsigned bits = __float_as_uint(fk.x * fk.x + fk.y * fk.y);
             const unsigned key = used ? 0u : ((bits & ~31u) | (unsigned)(31 - lane));
             const unsigned best = __reduce_max_sync(0xffffffffu, key);
@@ -487,16 +495,16 @@ static __device__ void leaf32(float2 *a, int ld, float2 *scr, int *flags) {
     bool used = false;
     int mystep = 0;
     stage(0, 0, false);
-    bar4();
+    bar();
     for (int k = 0; k < 32; ++k) {
         const int buf = k & 1;
         const int p = pp[buf];
         const float2 *cur = scr + buf * 32 * LEAF_SP;
         const float2 fk = cur[lane * LEAF_SP + k], d = cur[p * LEAF_SP + k];
-        float2 rr[8];
+        float2 rr[CW];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float4 q = reinterpret_cast<const float4 *>(cur + p * LEAF_SP + 8 * w)[j];
+        for (int j = 0; j < CW / 2; ++j) {
+            const float4 q = reinterpret_cast<const float4 *>(cur + p * LEAF_SP + CW * w)[j];
             rr[2 * j] = make_float2(q.x, q.y);
             rr[2 * j + 1] = make_float2(q.z, q.w);
         }
@@ -510,10 +518,10 @@ static __device__ void leaf32(float2 *a, int ld, float2 *scr, int *flags) {
         const float2 fe = isp ? make_float2(-1.f, 0.f) : fk;
         const float keep = isp ? 0.f : 1.f;
         const float2 ck = make_float2(-(fe.x * inv.x - fe.y * inv.y), -(fe.x * inv.y + fe.y * inv.x));
-        const bool own = w == (k >> 3);
-        const int kl = k & 7;
+        const bool own = w == k / CW;
+        const int kl = k % CW;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < CW; ++j) {
             const float2 r = rr[j];
             const float2 n = make_float2(r.x * inv.x - r.y * inv.y, r.x * inv.y + r.y * inv.x);
             float2 v;
@@ -522,12 +530,14 @@ static __device__ void leaf32(float2 *a, int ld, float2 *scr, int *flags) {
             x[j] = (own && j == kl) ? ck : v;
         }
         if (k + 1 < 32) stage(buf ^ 1, k + 1, used);
-        bar4();
+        bar();
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[mystep * ld + piv[8 * w + j]] = x[j];
-    bar4();
+    for (int j = 0; j < CW; ++j) a[mystep * ld + piv[CW * w + j]] = x[j];
+    bar();
 }
+
+static __device__ void leaf32(float2 *a, int ld, float2 *scr, int *flags) { leaf32t<8>(a, ld, scr, flags); }
 
 // Symmetric 2x2 recursion on the n x n block at `a` (n = 32 or 64) with
 // temporaries T, V (pitch P32) and the leaf scratch W.
@@ -606,20 +616,21 @@ static __device__ void leaf128_recursive(float *re, float *im, long long ld, int
     // inverse to a fixed unit-modulus probe v and compare X (X^-1 v) with v.
     // Above 2e-5 relative residual (a sound block gives a few 1e-7) the block
     // is inverted again by Gauss-Jordan with pivoting over all 128 rows.
-    __shared__ float2 s_y[128];
+    __shared__ float2 s_y[128], s_v[128];
     __shared__ float s_part[rec::NT / 32];
     __shared__ int s_bad;
     {
         const int t = threadIdx.x, r = t >> 2, sub = t & 3;
-        auto probe = [](int i) {
+        if (t < 128) {
             float sn, cs;
-            sincosf(2.3999632f * (float)i, &sn, &cs);
-            return make_float2(cs, sn);
-        };
+            sincosf(2.3999632f * (float)t, &sn, &cs);
+            s_v[t] = make_float2(cs, sn);
+        }
+        __syncthreads();
         float2 y = make_float2(0.f, 0.f);
         for (int q = 0; q < 32; ++q) {
             const int c = sub + 4 * q;
-            const float2 m = M[r * rec::P128 + c], v = probe(c);
+            const float2 m = M[r * rec::P128 + c], v = s_v[c];
             y.x += m.x * v.x - m.y * v.y;
             y.y += m.x * v.y + m.y * v.x;
         }
@@ -663,7 +674,7 @@ static __device__ void leaf128_recursive(float *re, float *im, long long ld, int
         z.y += __shfl_xor_sync(0xffffffffu, z.y, 2);
         float e2 = 0.f;
         if (sub == 0) {
-            const float2 v = probe(r);
+            const float2 v = s_v[r];
             e2 = (z.x - v.x) * (z.x - v.x) + (z.y - v.y) * (z.y - v.y);
         }
 #pragma unroll
