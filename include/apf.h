@@ -198,6 +198,17 @@ int apf_ridge_grad(apf_ctx *ctx, const double *grad_eps, double *grad_edges, voi
    ridges in air) up to ~25 to reach 1e-10. */
 int apf_set_refinement(apf_ctx *ctx, double tol, int max_iters);
 
+/* Mixed mode: refine by restarted GMRES(m) instead of plain iterative
+   refinement (m = 0, the default).  The low-precision factorization is the
+   (right) preconditioner of GMRES, with one Krylov space per right-hand-side
+   column; each restart takes m preconditioner applications from the true
+   float64 residual, and apf_stats.refine_iters counts those applications.
+   It pays on high-contrast slabs, where plain refinement contracts slowly.
+   Allocates 2m + 1 field-sized buffers (h x (n_in + n_out) x nx complex128
+   each) with the workspace; changing m re-creates the workspace, so the
+   fields of an earlier solve are gone.  1 <= m <= 8, or 0. */
+int apf_set_krylov(apf_ctx *ctx, int m);
+
 int apf_get_stats(const apf_ctx *ctx, apf_stats *stats);
 
 /* Measurement support (no counterpart in the paper).  When enabled, every

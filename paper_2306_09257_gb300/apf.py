@@ -29,7 +29,7 @@ EXPORTS = ("apf_create", "apf_destroy", "apf_set_grid", "apf_set_eps", "apf_set_
            "apf_get_channels", "apf_solve_S", "apf_solve_S_grad", "apf_grad_from_gamma",
            "apf_set_refinement", "apf_get_stats", "apf_set_profiling", "apf_get_profile",
            "apf_solve_S_noalloc", "apf_last_error", "apf_version", "apf_set_ridges", "apf_ridge_grad",
-           "apf_substrate_orders", "apf_reflection", "apf_reverse_S",
+           "apf_substrate_orders", "apf_reflection", "apf_reverse_S", "apf_set_krylov",
            "apf_sno_create", "apf_sno_destroy", "apf_sno_num_params", "apf_sno_set_params",
            "apf_sno_get_params", "apf_sno_forward", "apf_sno_gradients", "apf_sno_train_step")
 
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.apf_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
     L.apf_solve_S_noalloc.argtypes = [i, i, i, i, d, ctypes.POINTER(PML), dp, i, i, d, d, ip, i, ip, i, dp, vp]
     L.apf_substrate_orders.argtypes = [vp, ip, ip]
+    L.apf_set_krylov.argtypes = [vp, i]
     L.apf_reflection.argtypes = [vp, ip, i, dp, vp]
     L.apf_reverse_S.argtypes = [vp, dp, vp]
     L.apf_set_ridges.argtypes = [vp, dp, i, i, d, d, i, i, d, d, dp]
@@ -250,6 +251,11 @@ class Solver:
 
     def set_refinement(self, tol: float, max_iters: int):
         self._check(self._L.apf_set_refinement(self._h, float(tol), int(max_iters)))
+
+    def set_krylov(self, m: int):
+        """Mixed mode: GMRES(m) refinement (0: plain refinement); see apf_set_krylov."""
+        self._check(self._L.apf_set_krylov(self._h, int(m)))
+        self.version += 1
 
     def _alloc_S(self):
         mi, mo = self.channels()

@@ -313,6 +313,18 @@ int apf_set_refinement(apf_ctx *c, double tol, int max_iters) {
     return APF_OK;
 }
 
+int apf_set_krylov(apf_ctx *c, int m) {
+    if (!c) return APF_EINVAL;
+    if (m < 0 || m > 8) return set_err(c, APF_EINVAL, "Krylov dimension %d must be in [0, 8]", m);
+    if (c->precision == APF_FP64) return set_err(c, APF_EINVAL, "GMRES refinement applies to the mixed mode only");
+    if (m == c->krylov_m) return APF_OK;
+    c->krylov_m = m;
+    if (c->ws_nx < 0) return APF_OK;  // allocated with the workspace at apf_set_channels
+    cudaSetDevice(c->device);
+    free_workspace(c);
+    return ensure_workspace(c);
+}
+
 int apf_set_profiling(apf_ctx *c, int enable) {
     if (!c) return APF_EINVAL;
     cudaSetDevice(c->device);

@@ -80,6 +80,7 @@ struct apf_ctx {
     // refinement
     double ir_tol = 1e-10;
     int ir_max = 40;
+    int krylov_m = 0;  // mixed mode: GMRES(m) refinement when > 0
     // workspace signature
     int ws_nx = -1, ws_ny = -1, ws_h = -1, ws_min = -1, ws_mout = -1;
     long long ws_bytes = 0;

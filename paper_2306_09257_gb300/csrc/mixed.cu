@@ -14,6 +14,7 @@
 #include "leaf.cuh"
 
 #include <algorithm>
+#include <complex>
 #include <stdio.h>
 #include <stdlib.h>
 #include <vector>
@@ -31,6 +32,10 @@ struct MixedWork {
     double2 *r = nullptr, *delta = nullptr;          // refinement buffers (h*ncol*nx)
     double2 *cb = nullptr, *ct = nullptr;            // circulant products on the boundary rows
     double *rnorm = nullptr;                         // ||R_c||^2, ||r_c||^2
+    int km = 0;                                      // GMRES(km) refinement (0: plain refinement)
+    double2 *KV = nullptr, *KZ = nullptr;            // Krylov basis (km+1 fields) and preconditioned vectors (km)
+    double2 *kdot = nullptr, *ky = nullptr;          // Gram-Schmidt coefficients (km+1)*km*ncol, update km*ncol
+    double *knrm = nullptr;                          // ||W_c||^2 per Arnoldi step, km*ncol
     std::vector<void *> allocs;
 };
 
@@ -482,7 +487,7 @@ __global__ void k_residual(GridDev g, const double *eps, const double2 *E, const
     if (j == 0) v = cadd(v, cb[(long long)c * n + x]);
     if (j == g.h - 1) v = cadd(v, ct[(long long)c * n + x]);
     long long idx = j * L + (long long)c * n + x;
-    r[idx] = csub(R[idx], v);
+    r[idx] = R ? csub(R[idx], v) : v;  // without R: K E
 }
 
 // out[c] = sum_{j,x} |X_j[c][x]|^2 (one block per column, fixed order).
@@ -501,6 +506,41 @@ __global__ void k_colnorm(const double2 *X, int h, int ncol, int nx, double *out
         __syncthreads();
     }
     if (threadIdx.x == 0) out[c] = red[0];
+}
+
+// Krylov helpers over fields [row][column][x]: per-column dot products
+// (conj(A) . B, one block per column, fixed order), Y += sgn coef[c] X, and
+// Y = X / sqrt(nrm2[c]) (zero when the norm is zero).
+__global__ void k_coldot(const double2 *A, const double2 *B, int h, int ncol, int nx, double2 *out) {
+    __shared__ double2 red[256];
+    const int c = blockIdx.x;
+    double2 acc = cmk(0.0, 0.0);
+    for (int j = 0; j < h; ++j) {
+        const long long o = ((long long)j * ncol + c) * nx;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) acc = cadd(acc, cmul(cconj(A[o + x]), B[o + x]));
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + off]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0];
+}
+
+__global__ void k_colaxpy(double2 *Y, const double2 *X, const double2 *coef, double sgn, int ncol, int nx) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y, j = blockIdx.z;
+    if (x >= nx) return;
+    const long long i = ((long long)j * ncol + c) * nx + x;
+    Y[i] = cadd(Y[i], cscale(cmul(coef[c], X[i]), sgn));
+}
+
+__global__ void k_colscale(double2 *Y, const double2 *X, const double *nrm2, int ncol, int nx) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y, j = blockIdx.z;
+    if (x >= nx) return;
+    const long long i = ((long long)j * ncol + c) * nx + x;
+    const double n2 = nrm2[c];
+    Y[i] = n2 > 0.0 ? cscale(X[i], 1.0 / sqrt(n2)) : cmk(0.0, 0.0);
 }
 
 __global__ void k_axpy(double2 *E, const double2 *d, long long n) {
@@ -779,6 +819,14 @@ int mixed_alloc(apf_ctx *c) {
     WA(w->r, h * ncol * n); WA(w->delta, h * ncol * n);
     WA(w->cb, ncol * n); WA(w->ct, ncol * n);
     WA(w->rnorm, 2 * ncol);
+    w->km = c->krylov_m;
+    if (w->km > 0) {
+        WA(w->KV, (long long)(w->km + 1) * h * ncol * n);
+        WA(w->KZ, (long long)w->km * h * ncol * n);
+        WA(w->kdot, (long long)(w->km + 1) * w->km * ncol);
+        WA(w->ky, (long long)w->km * ncol);
+        WA(w->knrm, (long long)w->km * ncol);
+    }
 #undef WA
     return APF_OK;
 }
@@ -832,16 +880,149 @@ static int correct_body(apf_ctx *c, cudaStream_t s) {
     return APF_OK;
 }
 
-// Float64 iterative refinement: r = R - K E, E += Khat^-1 r until
-// max_c ||r_c|| / ||R_c|| <= tol (or max_iters corrections).
 // Diagnostics: APF_IR_VERBOSE=1 prints the residual of every refinement step.
 static const bool g_ir_verbose = [] {
     const char *e = getenv("APF_IR_VERBOSE");
     return e && e[0] == '1';
 }();
 
+// K E (the slab operator in float64) into out.
+static int apply_K(apf_ctx *c, const double2 *E, double2 *out, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    const int ncol = c->nin + c->nout, nx = c->nx;
+    const long long L = (long long)ncol * nx;
+    int logn = 0;
+    while ((1 << logn) < nx) ++logn;
+    const int threads = nx / 2 < 256 ? nx / 2 : 256;
+    const int smem = nx * (int)sizeof(double2);
+    APF_LAUNCH(c, k_circ_apply, ncol, threads, smem, s, E, w->cb, nx, logn, c->d_modes, c->d_tw);
+    APF_LAUNCH(c, k_circ_apply, ncol, threads, smem, s, E + (c->h - 1) * L, w->ct, nx, logn, c->d_modes + nx,
+               c->d_tw);
+    GridDev g = make_grid(c);
+    dim3 grid((nx + 255) / 256, ncol, c->h);
+    APF_LAUNCH(c, k_residual, grid, 256, 0, s, g, c->d_eps, E, (const double2 *)nullptr, w->cb, w->ct, out, ncol);
+    return APF_OK;
+}
+
+// min || beta e1 - H y || for one column by complex Givens rotations; H is
+// (m+1) x m upper Hessenberg, H[i][j] at h[i * m + j].
+static void hessenberg_lsq(int m, std::vector<std::complex<double>> &h, double beta, std::complex<double> *y) {
+    std::vector<std::complex<double>> g(m + 1, 0.0), cs(m), sn(m);
+    std::vector<double> cr(m);
+    g[0] = beta;
+    for (int j = 0; j < m; ++j) {
+        for (int i = 0; i < j; ++i) {
+            const std::complex<double> a = h[i * m + j], b = h[(i + 1) * m + j];
+            h[i * m + j] = cr[i] * a + sn[i] * b;
+            h[(i + 1) * m + j] = -std::conj(sn[i]) * a + cr[i] * b;
+        }
+        const std::complex<double> a = h[j * m + j], b = h[(j + 1) * m + j];
+        const double na = std::abs(a), nb = std::abs(b);
+        if (nb == 0.0) {
+            cr[j] = 1.0; sn[j] = 0.0;
+        } else if (na == 0.0) {
+            cr[j] = 0.0; sn[j] = std::conj(b) / nb;
+        } else {
+            const double nr = std::sqrt(na * na + nb * nb);
+            cr[j] = na / nr;
+            sn[j] = (a / na) * std::conj(b) / nr;
+        }
+        h[j * m + j] = cr[j] * a + sn[j] * b;
+        h[(j + 1) * m + j] = 0.0;
+        const std::complex<double> g0 = g[j], g1 = g[j + 1];
+        g[j] = cr[j] * g0 + sn[j] * g1;
+        g[j + 1] = -std::conj(sn[j]) * g0 + cr[j] * g1;
+    }
+    for (int j = m - 1; j >= 0; --j) {
+        std::complex<double> t = g[j];
+        for (int k = j + 1; k < m; ++k) t -= h[j * m + k] * y[k];
+        y[j] = std::abs(h[j * m + j]) > 0.0 ? t / h[j * m + j] : 0.0;
+    }
+}
+
+// Float64 refinement by restarted GMRES(m), right-preconditioned by the
+// low-precision factorization Khat^-1 (a fixed linear operator), one Krylov
+// space per right-hand-side column: from the true residual r = R - K E,
+// V_0 = r / ||r||; Z_j = Khat^-1 V_j, W = K Z_j orthogonalised against
+// V_0..V_j (modified Gram-Schmidt, per-column coefficients kept on the
+// device), V_{j+1} = W / ||W||; then E += sum_j y_j Z_j with y the
+// per-column least-squares solution of the (m+1) x m Hessenberg system.
+// The stopping rule and the iteration count (preconditioner applications)
+// are those of the plain refinement.
+static int mixed_refine_gmres(apf_ctx *c, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    const int m = w->km, ncol = c->nin + c->nout, nx = c->nx;
+    const long long L = (long long)c->h * ncol * nx;
+    const dim3 fgrid((nx + 255) / 256, ncol, c->h);
+    std::vector<double> nr(ncol), ne(ncol), hn((size_t)m * ncol);
+    std::vector<double2> hd((size_t)(m + 1) * m * ncol), yh((size_t)m * ncol);
+    std::vector<std::complex<double>> H((size_t)(m + 1) * m), y(m);
+    int iters = 0, rc, rising = 0;
+    double ratio = 0.0, prev = INFINITY;
+    cudaMemcpyAsync(nr.data(), w->rnorm, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
+    for (;;) {
+        residual(c, c->d_E, w->r, s);
+        APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, nx, w->rnorm + ncol);
+        cudaMemcpyAsync(ne.data(), w->rnorm + ncol, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return check_cuda(c, e, "refinement");
+        if (c->prof_on && iters == 0) prof_collect_range(c, c->g_main.prof_lo, c->g_main.prof_hi);
+        ratio = 0.0;
+        for (int i = 0; i < ncol; ++i) ratio = std::max(ratio, sqrt(ne[i] / std::max(nr[i], 1e-300)));
+        if (g_ir_verbose)
+            fprintf(stderr, "apf refinement (GMRES(%d)): %d preconditioner applications, max relative residual %.3e\n",
+                    m, iters, ratio);
+        if (!(ratio == ratio)) { ratio = INFINITY; break; }
+        if (ratio <= c->ir_tol || iters >= c->ir_max) break;
+        rising = ratio > prev ? rising + 1 : 0;
+        if (rising >= 2) break;
+        prev = ratio;
+        // Arnoldi on K Khat^-1 from V_0 = r / ||r||
+        APF_LAUNCH(c, k_colscale, fgrid, 256, 0, s, w->KV, w->r, w->rnorm + ncol, ncol, nx);
+        for (int j = 0; j < m; ++j) {
+            double2 *Vj = w->KV + j * L, *Wn = w->KV + (j + 1) * L, *Zj = w->KZ + j * L;
+            if ((rc = approx_solve(c, Vj, Zj, ncol, s))) return rc;
+            apply_K(c, Zj, Wn, s);
+            for (int i = 0; i <= j; ++i) {
+                double2 *hij = w->kdot + ((long long)j * (m + 1) + i) * ncol;
+                APF_LAUNCH(c, k_coldot, ncol, 256, 0, s, w->KV + i * L, Wn, c->h, ncol, nx, hij);
+                APF_LAUNCH(c, k_colaxpy, fgrid, 256, 0, s, Wn, w->KV + i * L, hij, -1.0, ncol, nx);
+            }
+            APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, Wn, c->h, ncol, nx, w->knrm + (long long)j * ncol);
+            APF_LAUNCH(c, k_colscale, fgrid, 256, 0, s, Wn, Wn, w->knrm + (long long)j * ncol, ncol, nx);
+        }
+        cudaMemcpyAsync(hd.data(), w->kdot, sizeof(double2) * hd.size(), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hn.data(), w->knrm, sizeof(double) * hn.size(), cudaMemcpyDeviceToHost, s);
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return check_cuda(c, e, "arnoldi");
+        for (int col = 0; col < ncol; ++col) {
+            std::fill(H.begin(), H.end(), std::complex<double>(0.0, 0.0));
+            for (int j = 0; j < m; ++j) {
+                for (int i = 0; i <= j; ++i) {
+                    const double2 v = hd[((size_t)j * (m + 1) + i) * ncol + col];
+                    H[(size_t)i * m + j] = std::complex<double>(v.x, v.y);
+                }
+                H[(size_t)(j + 1) * m + j] = std::sqrt(std::max(hn[(size_t)j * ncol + col], 0.0));
+            }
+            hessenberg_lsq(m, H, std::sqrt(std::max(ne[col], 0.0)), y.data());
+            for (int j = 0; j < m; ++j) yh[(size_t)j * ncol + col] = make_double2(y[j].real(), y[j].imag());
+        }
+        cudaMemcpyAsync(w->ky, yh.data(), sizeof(double2) * yh.size(), cudaMemcpyHostToDevice, s);
+        for (int j = 0; j < m; ++j)
+            APF_LAUNCH(c, k_colaxpy, fgrid, 256, 0, s, c->d_E, w->KZ + j * L, w->ky + (long long)j * ncol, 1.0,
+                       ncol, nx);
+        iters += m;
+    }
+    c->stats.refine_iters = iters;
+    c->stats.residual = ratio;
+    return ratio <= c->ir_tol ? APF_OK : APF_ENOCONV;
+}
+
+// Float64 iterative refinement: r = R - K E, E += Khat^-1 r until
+// max_c ||r_c|| / ||R_c|| <= tol (or max_iters corrections).
 int mixed_refine(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
+    if (w->km > 0) return mixed_refine_gmres(c, s);
     int ncol = (c->nin + c->nout);
     std::vector<double> nr(ncol), ne(ncol);
     int iters = 0, rc, rising = 0;
