@@ -100,7 +100,11 @@ int apf_set_ridges(apf_ctx *c, const double *edges, int n_edges, int mirror, dou
     cudaSetDevice(c->device);
     std::vector<double> t(n_edges);
     if (is_device_ptr(edges)) {
-        cudaError_t e = cudaMemcpy(t.data(), edges, sizeof(double) * n_edges, cudaMemcpyDeviceToHost);
+        // set-up runs on the context's own stream (no legacy-stream work that
+        // another thread's graph capture would forbid)
+        cudaError_t e = cudaMemcpyAsync(t.data(), edges, sizeof(double) * n_edges, cudaMemcpyDeviceToHost,
+                                        c->cap_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap_stream);
         if (e != cudaSuccess) return check_cuda(c, e, "read edges");
     } else {
         for (int i = 0; i < n_edges; ++i) t[i] = edges[i];
@@ -130,7 +134,8 @@ int apf_set_ridges(apf_ctx *c, const double *edges, int n_edges, int mirror, dou
     rc = apf_set_eps(c, c->d_ridge_eps, j0, h, eps_sub, eps_clad);
     if (rc) return rc;
     if (eps_out) {
-        e = cudaMemcpy(eps_out, c->d_ridge_eps, sizeof(double) * n, cudaMemcpyDefault);
+        e = cudaMemcpyAsync(eps_out, c->d_ridge_eps, sizeof(double) * n, cudaMemcpyDefault, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return check_cuda(c, e, "eps_out");
     }
     return APF_OK;
