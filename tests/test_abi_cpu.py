@@ -3,6 +3,9 @@ symbol that include/apf.h declares, and refuses to run without a device."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
+import tempfile
 
 import pytest
 
@@ -56,3 +59,26 @@ def test_null_context_calls(lib):
     assert lib.apf_set_grid(None, 64, 100, 20, 20, 16.0, None) == apf.APF_EINVAL
     assert lib.apf_solve_S(None, None, None) == apf.APF_EINVAL
     lib.apf_destroy(None)
+
+
+def test_new_entry_points_reject_null_context(lib):
+    assert lib.apf_set_ridges(None, None, 0, 1, 4.0, 1.0, -1, 1, 2.25, 1.0, None) == apf.APF_EINVAL
+    assert lib.apf_ridge_grad(None, None, None, None) == apf.APF_EINVAL
+    assert lib.apf_reflection(None, None, 0, None, None) == apf.APF_EINVAL
+    assert lib.apf_reverse_S(None, None, None) == apf.APF_EINVAL
+    assert lib.apf_substrate_orders(None, None, None) == apf.APF_EINVAL
+    assert lib.apf_set_krylov(None, 2) == apf.APF_EINVAL
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="no C compiler")
+def test_headers_compile_as_plain_c():
+    """The public headers are plain C (no C++ or torch types): a C99 file that
+    includes both compiles."""
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "use.c")
+        with open(src, "w") as f:
+            f.write('#include "apf.h"\n#include "apf_surrogate.h"\n'
+                    "int main(void) { apf_stats st; apf_profile pr; (void)st; (void)pr; return apf_version() < 0; }\n")
+        r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", os.path.join(ROOT, "include"),
+                            src], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
