@@ -50,7 +50,16 @@ def test_layout_has_no_grazing_orders():
 
 def thomas_1d(pb, m, eps_slab_value):
     """Tridiagonal problem along y for Fourier order m, written from the
-    operator's definition and solved with LAPACK gbsv (solve_banded)."""
+    operator's definition and solved with LAPACK gbsv (solve_banded); returns
+    the projection on the output row."""
+    e = field_1d(pb, m, eps_slab_value)
+    _, nu_out = O.ky_nu(pb.nx, pb.k, pb.eps_clad, [m])
+    return math.sqrt(nu_out[0]) * e[pb.j_out]
+
+
+def field_1d(pb, m, eps_slab_value):
+    """The field along y of the decoupled 1-D problem of Fourier order m for
+    a unit-flux source on the source row."""
     ny, k = pb.ny, pb.k
     lam_m = 2.0 - 2.0 * math.cos(2.0 * math.pi * m / pb.nx)
     eps = np.full(ny, pb.eps_sub)
@@ -65,9 +74,7 @@ def thomas_1d(pb, m, eps_slab_value):
     rhs = np.zeros(ny, complex)
     _, nu_in = O.ky_nu(pb.nx, k, pb.eps_sub, [m])
     rhs[pb.j_src] = -2j * math.sqrt(nu_in[0])
-    e = solve_banded((1, 1), ab, rhs)
-    _, nu_out = O.ky_nu(pb.nx, k, pb.eps_clad, [m])
-    return math.sqrt(nu_out[0]) * e[pb.j_out]
+    return solve_banded((1, 1), ab, rhs)
 
 
 def test_uniform_slab_matches_1d_banded_solve():
@@ -79,6 +86,22 @@ def test_uniform_slab_matches_1d_banded_solve():
     assert np.max(np.abs(np.diag(S) - diag)) < 1e-12 * np.max(np.abs(diag)) + 1e-13
     off = S - np.diag(np.diag(S))
     assert np.max(np.abs(off)) < 1e-12
+
+
+def test_uniform_slab_reflection_matches_1d_banded_solve():
+    """The reflection block of a uniform slab is diagonal, and each entry is
+    the decoupled 1-D problem's source-row field, projected with the
+    substrate flux normalisation, minus the incident wave."""
+    pb = small_problem(eps_slab=np.full((4, 32), 3.1))
+    sol = O.solve_S(pb)
+    m = pb.inputs()
+    R = O.reflection(sol, m)
+    _, nu = O.ky_nu(pb.nx, pb.k, pb.eps_sub, m)
+    diag = np.array([math.sqrt(nu[i]) * field_1d(pb, int(mm), 3.1)[pb.j_src] - 1.0 for i, mm in enumerate(m)])
+    assert np.max(np.abs(np.diag(R) - diag)) < 1e-12 * max(1.0, np.max(np.abs(diag)))
+    assert np.max(np.abs(R - np.diag(np.diag(R)))) < 1e-12
+    # a slab of contrast 3.1 / 2.25 / 1 reflects measurably
+    assert np.min(np.abs(diag)) > 1e-3
 
 
 def test_homogeneous_medium_closed_form():
