@@ -135,6 +135,26 @@ def test_reciprocity():
             assert abs(Sr[pin[-int(ma)], pout[-int(mb)]] - S[b, a]) < 1e-12
 
 
+def test_reflection_reciprocity():
+    """A = A^T: the reflection block satisfies R(m_b <- m_a) = R(-m_a <- -m_b)
+    on a scattering slab (orders propagating in the substrate, a set closed
+    under m -> -m)."""
+    pb = small_problem(seed=4)
+    sol = O.solve_S(pb)
+    orders = O.propagating_orders(pb.nx, pb.k, pb.eps_sub)
+    R = O.reflection(sol, orders)
+    pin = {int(m): i for i, m in enumerate(pb.inputs())}
+    pref = {int(m): i for i, m in enumerate(orders)}
+    checked = 0
+    for b, mb in enumerate(orders):
+        for a, ma in enumerate(pb.inputs()):
+            if -int(mb) in pin:
+                assert abs(R[pref[-int(ma)], pin[-int(mb)]] - R[b, a]) < 1e-12
+                checked += 1
+    assert checked >= len(pb.inputs()) ** 2
+    assert np.max(np.abs(R)) > 1e-3  # the slab really reflects
+
+
 @pytest.mark.parametrize("shift", [1, 7])
 def test_cyclic_shift_invariant(shift):
     pb = small_problem(seed=2)
