@@ -118,3 +118,19 @@ def test_planted_mirror_sign_mistake_is_caught(monkeypatch):
 
     J = wrong(nx, e, True, EPS_R, EPS_B)
     assert not np.allclose(J, _fd_jacobian(nx, e, True, 1e-6), atol=1e-7, rtol=0)
+
+
+@pytest.mark.parametrize("mirror", [True, False])
+def test_ridge_edge_generator_contract(mirror):
+    """Input generator: sorted edges inside the half (or whole) period, every
+    gap and both end margins at least min_gap, reproducible per seed."""
+    for w in (W.TINY, W.MID, W.LARGE):
+        n = W.ridge_count(w)
+        e = W.ridge_edges(w.nx, n, 7, mirror=mirror)
+        lo, hi = -w.nx / 2.0, (0.0 if mirror else w.nx / 2.0)
+        assert e.shape == (2 * n,)
+        assert np.all(np.diff(e) >= 2.0 - 1e-12)
+        assert e[0] - lo >= 2.0 - 1e-12 and hi - e[-1] >= 2.0 - 1e-12
+        assert np.array_equal(e, W.ridge_edges(w.nx, n, 7, mirror=mirror))
+        assert not np.array_equal(e, W.ridge_edges(w.nx, n, 8, mirror=mirror))
+    assert (W.ridge_count(W.MID), W.ridge_count(W.LARGE)) == (40, 133)
