@@ -58,9 +58,12 @@ extern "C" {
 #define APF_ECUDA (-6)      /* CUDA runtime error */
 #define APF_ESTATE (-7)     /* call order: grid, permittivity or channels not set */
 
-/* Arithmetic of the slab elimination. */
+/* Arithmetic of the slab elimination (the paper factors in float64; the mixed
+   modes are this library's: low-precision products plus float64 refinement). */
 #define APF_FP64 0          /* everything in float64 */
-#define APF_MIXED_BF16X3 1  /* tensor-core bf16x3 products, fp32 accumulation,
+#define APF_MIXED_TF32 1    /* reserved: TF32 tensor-core products are not built;
+                               apf_create returns APF_EINVAL for it */
+#define APF_MIXED_BF16X3 2  /* tensor-core bf16x3 products, fp32 accumulation,
                                float64 iterative refinement of the fields */
 
 /* Objectives for apf_solve_S_grad (relative diffraction orders d = m_out - m_in). */
@@ -91,7 +94,12 @@ typedef struct {
 } apf_stats;
 
 /* Create a context on CUDA device `cuda_device` with APF_FP64 or
-   APF_MIXED_BF16X3 arithmetic.  *out receives the handle (NULL on failure). */
+   APF_MIXED_BF16X3 arithmetic.  *out receives the handle (NULL on failure).
+   The context stands for one instance of the paper's problem (Sec. 2, first
+   paragraph: the operator A, the inputs B and the outputs C of one
+   structure); it owns every device array the solves need.  APF_EINVAL for an
+   unknown precision or a device index out of range, APF_ECUDA without a
+   CUDA device; the mixed mode also needs an sm_103 GPU (APF_EINVAL). */
 int apf_create(apf_ctx **out, int cuda_device, int precision);
 
 /* Free the context and its device workspace.  NULL is a no-op. */
@@ -103,11 +111,19 @@ void apf_destroy(apf_ctx *ctx);
 int apf_set_grid(apf_ctx *ctx, int nx, int ny, int npml_bot, int npml_top,
                  double lambda_px, const apf_pml_params *pml);
 
-/* Design slab and background media.  eps_slab: h*nx float64, [row][x],
-   host or device, real and finite.  j0 < 0 centres the slab between the
-   PMLs; otherwise the source row npml_bot < j0 and j0+h <= ny-npml_top-1. */
+/* Design slab and background media: the relative permittivity eps_r(r)
+   that the operator A of paper Sec. 2 contains (-k^2 eps on its diagonal),
+   with the design variables p_k of Eq. 1 being the slab pixels.
+   eps_slab: h*nx float64, [row][x], host or device, real and finite
+   (APF_EINVAL otherwise, before anything is changed).  j0 < 0 centres the
+   slab between the PMLs; otherwise the source row npml_bot < j0 and
+   j0+h <= ny-npml_top-1.  A device-resident eps_slab is read in order on
+   `stream` (a cudaStream_t, NULL = the legacy default stream): pass the
+   stream whose work produced it; the call synchronizes that stream before it
+   returns, so the caller may then reuse or free eps_slab.  Host arrays are
+   copied before return as well. */
 int apf_set_eps(apf_ctx *ctx, const double *eps_slab, int j0, int h,
-                double eps_sub, double eps_clad);
+                double eps_sub, double eps_clad, void *stream);
 
 /* Channel orders (host int arrays).  NULL (or n = 0) selects every order
    that propagates in the cladding (paper Sec. 3: all angles within the range
@@ -120,8 +136,12 @@ int apf_set_channels(apf_ctx *ctx, const int *m_in, int n_in,
    orders (n_in resp. n_out ints). */
 int apf_get_channels(const apf_ctx *ctx, int *n_in, int *n_out, int *m_in, int *m_out);
 
-/* S = C A^-1 B (n_out x n_in complex128, [b][a]).  Keeps the slab fields so
-   that apf_grad_from_gamma can follow. */
+/* S = C A^-1 B (n_out x n_in complex128, [b][a]): the scattering matrix of
+   paper Sec. 2 (first paragraph; D = 0 for transmission), all input and
+   output channels from one elimination.  Keeps the slab fields so that
+   apf_grad_from_gamma can follow.  APF_ESTATE before apf_set_grid,
+   apf_set_eps and apf_set_channels; APF_ENOCONV (mixed mode) returns S
+   from a refinement that stopped above its tolerance. */
 int apf_solve_S(apf_ctx *ctx, double *S, void *stream);
 
 /* S, f and df/deps (h*nx float64) for a built-in objective.
@@ -175,10 +195,12 @@ int apf_reverse_S(apf_ctx *ctx, double *S_rev, void *stream);
    treatment; this linear one is continuous in every edge.  The slab is then
    set exactly as apf_set_eps(ctx, eps, j0, h, eps_sub, eps_clad) would;
    eps_out (h*nx, host or device, may be NULL) receives it.  Requires
-   apf_set_grid; APF_EINVAL for unsorted, out-of-range or non-finite edges. */
+   apf_set_grid; APF_EINVAL for unsorted, out-of-range or non-finite edges.
+   Device-resident edges are read, and eps_out is written, in order on
+   `stream` (as for apf_set_eps); the call synchronizes it before returning. */
 int apf_set_ridges(apf_ctx *ctx, const double *edges, int n_edges, int mirror,
                    double eps_ridge, double eps_bg, int j0, int h,
-                   double eps_sub, double eps_clad, double *eps_out);
+                   double eps_sub, double eps_clad, double *eps_out, void *stream);
 
 /* Chain rule from a pixel gradient to the edges of the last apf_set_ridges:
    df/dt_k = sum_{rows, x} (df/deps)[row][x] * deps_x/dt_k, where deps_x/dt_k
@@ -209,6 +231,10 @@ int apf_set_refinement(apf_ctx *ctx, double tol, int max_iters);
    fields of an earlier solve are gone.  1 <= m <= 8, or 0. */
 int apf_set_krylov(apf_ctx *ctx, int m);
 
+/* Statistics of the last solve: refinement sweeps and residual, device time
+   per stage of the pipeline (the stages mirror the paper's breakdown of APF
+   time into factorization and post-processing, Supplement Table S1), kernel
+   launches and the workspace size.  *stats is written; APF_EINVAL for NULL. */
 int apf_get_stats(const apf_ctx *ctx, apf_stats *stats);
 
 /* Measurement support (no counterpart in the paper).  When enabled, every

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libapf.so")
 
 APF_OK, APF_EINVAL, APF_ENOMEM, APF_ESINGULAR = 0, -1, -2, -3
 APF_ENOCONV, APF_ETIMEOUT, APF_ECUDA, APF_ESTATE = -4, -5, -6, -7
-APF_FP64, APF_MIXED_BF16X3 = 0, 1
+APF_FP64, APF_MIXED_TF32, APF_MIXED_BF16X3 = 0, 1, 2  # TF32 is reserved (not built)
 APF_OBJ_POWER, APF_OBJ_SPLITTER = 1, 2
 
 PRECISIONS = {"fp64": APF_FP64, "mixed": APF_MIXED_BF16X3, "bf16x3": APF_MIXED_BF16X3}
@@ -80,7 +80,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.apf_destroy.argtypes = [vp]
     L.apf_destroy.restype = None
     L.apf_set_grid.argtypes = [vp, i, i, i, i, d, ctypes.POINTER(PML)]
-    L.apf_set_eps.argtypes = [vp, dp, i, i, d, d]
+    L.apf_set_eps.argtypes = [vp, dp, i, i, d, d, vp]
     L.apf_set_channels.argtypes = [vp, ip, i, ip, i]
     L.apf_get_channels.argtypes = [vp, ip, ip, ip, ip]
     L.apf_solve_S.argtypes = [vp, dp, vp]
@@ -95,7 +95,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.apf_set_krylov.argtypes = [vp, i]
     L.apf_reflection.argtypes = [vp, ip, i, dp, vp]
     L.apf_reverse_S.argtypes = [vp, dp, vp]
-    L.apf_set_ridges.argtypes = [vp, dp, i, i, d, d, i, i, d, d, dp]
+    L.apf_set_ridges.argtypes = [vp, dp, i, i, d, d, i, i, d, d, dp, vp]
     L.apf_ridge_grad.argtypes = [vp, dp, dp, vp]
     L.apf_last_error.argtypes = [vp]
     L.apf_last_error.restype = ctypes.c_char_p
@@ -166,8 +166,9 @@ class Solver:
         h = int(eps_slab.shape[0])
         if isinstance(eps_slab, np.ndarray):
             eps_slab = np.ascontiguousarray(eps_slab, dtype=np.float64)
+        # a CUDA tensor is read in order on torch's current stream (after the ops that wrote it)
         self._check(self._L.apf_set_eps(self._h, _ptr(eps_slab, np.float64), int(j0), h,
-                                        float(eps_sub), float(eps_clad)))
+                                        float(eps_sub), float(eps_clad), _stream_of(eps_slab)))
         self.h = h
         self.version += 1
 
@@ -186,7 +187,8 @@ class Solver:
             eps_p = _ptr(eps, np.float64)
         self._check(self._L.apf_set_ridges(self._h, _ptr(edges, np.float64), int(edges.shape[0]),
                                            1 if mirror else 0, float(eps_ridge), float(eps_bg), int(j0), int(h),
-                                           float(eps_sub), float(eps_clad), eps_p))
+                                           float(eps_sub), float(eps_clad), eps_p,
+                                           _stream_of(edges, eps if eps_out is not None else None)))
         self.h = int(h)
         self.n_edges = int(edges.shape[0])
         self.version += 1

@@ -136,11 +136,13 @@ static double disp_q(const apf_ctx *c, int m, double eps) {
 
 extern "C" {
 
-int apf_version(void) { return (1 << 16) | 1; }
+int apf_version(void) { return (2 << 16) | 0; }
 
 int apf_create(apf_ctx **out, int cuda_device, int precision) {
     if (!out) return set_err(nullptr, APF_EINVAL, "apf_create: out is NULL");
     *out = nullptr;
+    if (precision == APF_MIXED_TF32)
+        return set_err(nullptr, APF_EINVAL, "apf_create: APF_MIXED_TF32 is reserved (not built); use APF_MIXED_BF16X3");
     if (precision != APF_FP64 && precision != APF_MIXED_BF16X3)
         return set_err(nullptr, APF_EINVAL, "apf_create: unknown precision %d", precision);
     int ndev = 0;
@@ -211,7 +213,7 @@ int apf_set_grid(apf_ctx *c, int nx, int ny, int npml_bot, int npml_top, double 
     return APF_OK;
 }
 
-int apf_set_eps(apf_ctx *c, const double *eps_slab, int j0, int h, double eps_sub, double eps_clad) {
+int apf_set_eps(apf_ctx *c, const double *eps_slab, int j0, int h, double eps_sub, double eps_clad, void *stream) {
     if (!c) return APF_EINVAL;
     if (!c->grid_set) return set_err(c, APF_ESTATE, "apf_set_eps before apf_set_grid");
     if (!eps_slab) return set_err(c, APF_EINVAL, "eps_slab is NULL");
@@ -226,28 +228,32 @@ int apf_set_eps(apf_ctx *c, const double *eps_slab, int j0, int h, double eps_su
     if (eps_clad > eps_sub) return set_err(c, APF_EINVAL, "eps_clad > eps_sub: cladding orders would not all propagate in the substrate");
     cudaSetDevice(c->device);
     long long n = (long long)h * c->nx;
+    const bool on_dev = is_device_ptr(eps_slab);
+    // a device array is read in order on the caller's stream (after the work
+    // that produced it); host arrays go through the context's own stream
+    cudaStream_t s = on_dev ? (cudaStream_t)stream : c->cap_stream;
+    std::vector<double> tmp;
+    const double *hv = eps_slab;
+    if (on_dev) {
+        tmp.resize(n);
+        cudaError_t e = cudaMemcpyAsync(tmp.data(), eps_slab, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return check_cuda(c, e, "read eps");
+        hv = tmp.data();
+    }
+    for (long long i = 0; i < n; ++i)
+        if (!isfinite(hv[i])) return set_err(c, APF_EINVAL, "eps_slab[%lld] is not finite", i);
     if (c->h != h || !c->d_eps) {
         if (c->d_eps) cudaFree(c->d_eps);
         c->d_eps = nullptr;
         cudaError_t e = cudaMalloc(&c->d_eps, sizeof(double) * n);
         if (e != cudaSuccess) return check_cuda(c, e, "cudaMalloc eps");
     }
-    if (is_device_ptr(eps_slab)) {
-        std::vector<double> tmp(n);
-        cudaError_t e = cudaMemcpyAsync(tmp.data(), eps_slab, sizeof(double) * n, cudaMemcpyDeviceToHost, c->cap_stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap_stream);
-        if (e != cudaSuccess) return check_cuda(c, e, "read eps");
-        for (long long i = 0; i < n; ++i)
-            if (!isfinite(tmp[i])) return set_err(c, APF_EINVAL, "eps_slab[%lld] is not finite", i);
-        e = cudaMemcpyAsync(c->d_eps, eps_slab, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->cap_stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap_stream);
-        if (e != cudaSuccess) return check_cuda(c, e, "copy eps");
-    } else {
-        for (long long i = 0; i < n; ++i)
-            if (!isfinite(eps_slab[i])) return set_err(c, APF_EINVAL, "eps_slab[%lld] is not finite", i);
-        cudaError_t e = cudaMemcpyAsync(c->d_eps, eps_slab, sizeof(double) * n, cudaMemcpyHostToDevice, c->cap_stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap_stream);
-        if (e != cudaSuccess) return check_cuda(c, e, "upload eps");
+    {
+        cudaError_t e = cudaMemcpyAsync(c->d_eps, eps_slab, sizeof(double) * n,
+                                        on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return check_cuda(c, e, on_dev ? "copy eps" : "upload eps");
     }
     bool changed = (c->h != h) || (c->eps_sub != eps_sub) || (c->eps_clad != eps_clad);
     if (changed || c->j0 != j0) graphs_reset(c);

@@ -68,8 +68,10 @@ extern "C" int apf_solve_S_noalloc(int nx, int ny, int npml_bot, int npml_top, d
         if (b > 0 && m_out[b] <= m_out[b - 1]) return fail(APF_EINVAL, "output orders must be strictly ascending");
         ords_out[b] = m_out[b];
     }
+    cudaStream_t s = (cudaStream_t)stream;
     {
-        // the permittivity must be finite (checked on the host, from a stack copy if it is on the device)
+        // the permittivity must be finite (checked on the host, from a stack copy if it is on the device;
+        // the copy is read in order on the caller's stream, after the work that produced eps_slab)
         double tmp[kMaxH * kMaxNx];
         cudaPointerAttributes at;
         bool on_dev = cudaPointerGetAttributes(&at, eps_slab) == cudaSuccess &&
@@ -77,9 +79,12 @@ extern "C" int apf_solve_S_noalloc(int nx, int ny, int npml_bot, int npml_top, d
         cudaGetLastError();
         const double *src = eps_slab;
         if (on_dev) {
-            if (cudaMemcpy(tmp, eps_slab, sizeof(double) * h * nx, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaError_t e = cudaMemcpyAsync(tmp, eps_slab, sizeof(double) * h * nx, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
                 cudaGetLastError();
-                return fail(APF_ECUDA, "cannot read eps_slab");
+                return set_err(nullptr, APF_ECUDA, "apf_solve_S_noalloc: cannot read eps_slab: %s",
+                               cudaGetErrorString(e));
             }
             src = tmp;
         }
@@ -138,11 +143,14 @@ extern "C" int apf_solve_S_noalloc(int nx, int ny, int npml_bot, int npml_top, d
     c.d_flags = (int *)carve(sizeof(int) * 4);
     if (off > kScratchBytes) return fail(APF_EINVAL, "problem does not fit the scratch array");
     // ---- the pipeline (same kernels as apf_solve_S in APF_FP64) ----
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaMemcpyAsync(c.d_eps, eps_slab, sizeof(double) * h * n, cudaMemcpyDefault, s);
-    cudaMemcpyAsync(c.d_min, ords_in, sizeof(int) * n_in, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(c.d_mout, ords_out, sizeof(int) * n_out, cudaMemcpyHostToDevice, s);
-    cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), s);
+    cudaError_t ce = cudaMemcpyAsync(c.d_eps, eps_slab, sizeof(double) * h * n, cudaMemcpyDefault, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(c.d_min, ords_in, sizeof(int) * n_in, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(c.d_mout, ords_out, sizeof(int) * n_out, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c.d_flags, 0, 4 * sizeof(int), s);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(nullptr, APF_ECUDA, "apf_solve_S_noalloc: upload: %s", cudaGetErrorString(ce));
+    }
     launch_twiddles(&c, s);
     launch_boundary(&c, s);
     for (int j = 0; j < h; ++j) {
@@ -154,14 +162,24 @@ extern "C" int apf_solve_S_noalloc(int nx, int ny, int npml_bot, int npml_top, d
     launch_build_rhs(&c, c.d_E, s);
     fields64(&c, s);
     launch_readout(&c, s);
-    cudaMemcpyAsync(S, c.d_S, sizeof(double2) * n_in * n_out, cudaMemcpyDefault, s);
+    // a failed launch (configuration or resources) is reported here, before the
+    // sync, so that S is never taken from an earlier call's leftovers
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        return set_err(nullptr, APF_ECUDA, "apf_solve_S_noalloc: kernel launch: %s", cudaGetErrorString(ce));
+    }
+    ce = cudaMemcpyAsync(S, c.d_S, sizeof(double2) * n_in * n_out, cudaMemcpyDefault, s);
     int flags = 0;
-    cudaMemcpyAsync(&flags, c.d_flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&flags, c.d_flags, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = ce;
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_err(nullptr, APF_ECUDA, "apf_solve_S_noalloc: %s", cudaGetErrorString(e));
     }
     if (flags & FLAG_SINGULAR) return fail(APF_ESINGULAR, "zero pivot in a diagonal-block inversion");
+    if (flags & FLAG_TIMEOUT) return fail(APF_ETIMEOUT, "a bounded device wait gave up");
+    if (flags & FLAG_NONFINITE) return fail(APF_ECUDA, "non-finite value in the elimination");
     return APF_OK;
 }

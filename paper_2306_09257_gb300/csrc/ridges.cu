@@ -89,7 +89,7 @@ void ridges_free(apf_ctx *c) {
 extern "C" {
 
 int apf_set_ridges(apf_ctx *c, const double *edges, int n_edges, int mirror, double eps_ridge, double eps_bg,
-                   int j0, int h, double eps_sub, double eps_clad, double *eps_out) {
+                   int j0, int h, double eps_sub, double eps_clad, double *eps_out, void *stream) {
     if (!c) return APF_EINVAL;
     if (!c->grid_set) return set_err(c, APF_ESTATE, "apf_set_ridges before apf_set_grid");
     if (!edges) return set_err(c, APF_EINVAL, "edges is NULL");
@@ -99,12 +99,11 @@ int apf_set_ridges(apf_ctx *c, const double *edges, int n_edges, int mirror, dou
         return set_err(c, APF_EINVAL, "ridge and background permittivities must be positive and finite");
     cudaSetDevice(c->device);
     std::vector<double> t(n_edges);
+    cudaStream_t caller = (cudaStream_t)stream;
     if (is_device_ptr(edges)) {
-        // set-up runs on the context's own stream (no legacy-stream work that
-        // another thread's graph capture would forbid)
-        cudaError_t e = cudaMemcpyAsync(t.data(), edges, sizeof(double) * n_edges, cudaMemcpyDeviceToHost,
-                                        c->cap_stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap_stream);
+        // device edges are read in order on the caller's stream, after the work that produced them
+        cudaError_t e = cudaMemcpyAsync(t.data(), edges, sizeof(double) * n_edges, cudaMemcpyDeviceToHost, caller);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(caller);
         if (e != cudaSuccess) return check_cuda(c, e, "read edges");
     } else {
         for (int i = 0; i < n_edges; ++i) t[i] = edges[i];
@@ -131,11 +130,13 @@ int apf_set_ridges(apf_ctx *c, const double *edges, int n_edges, int mirror, dou
     c->ridge_mirror = mirror ? 1 : 0;
     c->ridge_eps_r = eps_ridge;
     c->ridge_eps_b = eps_bg;
-    rc = apf_set_eps(c, c->d_ridge_eps, j0, h, eps_sub, eps_clad);
+    // the generated slab was written (and synchronized) on the context's own stream
+    rc = apf_set_eps(c, c->d_ridge_eps, j0, h, eps_sub, eps_clad, (void *)s);
     if (rc) return rc;
     if (eps_out) {
-        e = cudaMemcpyAsync(eps_out, c->d_ridge_eps, sizeof(double) * n, cudaMemcpyDefault, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        // written in order on the caller's stream (after its earlier work on eps_out)
+        e = cudaMemcpyAsync(eps_out, c->d_ridge_eps, sizeof(double) * n, cudaMemcpyDefault, caller);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(caller);
         if (e != cudaSuccess) return check_cuda(c, e, "eps_out");
     }
     return APF_OK;

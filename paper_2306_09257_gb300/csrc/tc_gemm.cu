@@ -311,23 +311,6 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
-__device__ __forceinline__ void tma_load_3d_mc(void *smem_dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
-                                               int c2, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(smem_dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
-}
-
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -338,65 +321,115 @@ __device__ __forceinline__ uint32_t cluster_rank() {
     return r;
 }
 
-// Two-CTA cluster variant: the CTAs of a cluster compute vertically adjacent
-// 128-row tiles that share one B tile; each CTA loads half of that B tile
-// with a cluster multicast into both CTAs' shared memory, and each MMA
-// completion is committed to the stage barriers of both CTAs (a stage is
-// refilled only when both have consumed it).  Halves the B traffic per SM.
-// FUSED (two split planes only): a stage holds both planes of the A and the
-// B tile of one k block, and the three retained plane products (x0 y0, x0 y1,
-// x1 y0) are issued from it, so each plane tile is loaded once instead of
-// once per product that uses it (4 tile loads per k block instead of 6).
-template <int BN, int STAGES, bool FUSED>
-struct McLayout {
-    static constexpr int PL = FUSED ? 2 : 1;  // planes per operand per stage
-    static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = BN * BK * 2;
-    static constexpr int STAGE = PL * (A_BYTES + B_BYTES);
+// Shared::cluster address of this CTA's variable `p` in cluster CTA `rank`.
+__device__ __forceinline__ uint32_t peer_addr(const void *p, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
+    return a;
+}
+
+// Arrive on an mbarrier given by its shared::cluster address (this CTA's or the peer's).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+// TMA load into this CTA's shared memory whose completion is signalled on the
+// mbarrier at shared::cluster address `bar`, which may be the peer CTA's
+// (.cta_group::2: the barrier sits in either CTA of the pair).
+__device__ __forceinline__ void tma_load_3d_pair(void *smem_dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                                 int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 "
+        "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(smem_dst)),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on the mbarrier at shared::cluster address `bar` once every MMA this
+// thread issued so far has completed (on both CTAs of the pair).
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Two-SM kernel (tcgen05 cta_group::2): a cluster of two CTAs computes one
+// 256 x BN output tile with M = 256 MMAs issued by the even CTA.  Each CTA
+// TMA-loads, into its own shared memory, its 128 rows of the A tile and its
+// BN/2 rows of the B tile (both bf16 split planes of one k block per stage),
+// so per SM the operand traffic per flop is half that of a one-CTA 128 x BN
+// tile and the same shared memory holds twice the k depth of look-ahead.
+// Each CTA's tensor memory holds the accumulator rows of its own 128 output
+// rows over all BN columns, and each CTA's epilogue stores them.
+//   full[s]   (even CTA): both CTAs' loads of stage s landed (tx bytes of both);
+//   empty[s]  (each CTA): the MMAs reading stage s finished (commit to both);
+//   tfull[b]  (each CTA): accumulator b is complete (commit to both);
+//   tempty[b] (even CTA): both CTAs' epilogues have drained accumulator b.
+// Planes: the three retained products x0 y0, x0 y1, x1 y0 are issued from
+// one stage, so every plane tile is loaded once per k block.
+template <int BN, int STAGES>
+struct PairLayout {
+    static constexpr int BNH = BN / 2;
+    static constexpr int A_PLANE = BM * BK * 2;
+    static constexpr int B_PLANE = BNH * BK * 2;
+    static constexpr int STAGE = 2 * (A_PLANE + B_PLANE);
     static constexpr int BAR = STAGES * STAGE;
     static constexpr int TOTAL = BAR + (2 * STAGES + 4) * 8 + 16 + 1024;
+    static_assert(B_PLANE % 1024 == 0, "B tile rows must fill whole 128-byte swizzle atoms");
+    static_assert(BN % 32 == 0 && BN >= 64 && BN <= 256, "MMA N for M = 256");
 };
 
-template <int BN, int STAGES, bool FUSED>
+constexpr int PAIR_TMEM_COLS = 512;
+
+template <int BN, int STAGES>
 __global__ void __launch_bounds__(192, 1)
-    k_tc_gemm_mc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
-    using L = McLayout<BN, STAGES, FUSED>;
+    k_tc_gemm_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+    using L = PairLayout<BN, STAGES>;
+    constexpr int BNH = L::BNH;
     extern __shared__ uint8_t smem_raw[];
+    // same offset in both CTAs: the MMA addresses both CTAs' tiles with one descriptor
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + L::BAR);
     uint64_t *empty = full + STAGES;
-    uint64_t *tfull = empty + STAGES;
-    uint64_t *tempty = tfull + 2;
+    uint64_t *tfull = empty + STAGES;  // [2]
+    uint64_t *tempty = tfull + 2;      // [2]
     uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rank = (int)cluster_rank();
-    const int Mt = (p.M + BM - 1) / BM, Mp = (Mt + 1) / 2, Nt = (p.N + BN - 1) / BN;
-    const int npairs = Mp * Nt;
-    const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
-    const int total = FUSED ? p.kblocks : p.nseg * p.kblocks;
-    constexpr int HALF = BN / 2;
-    constexpr int HALF_BYTES = HALF * BK * 2;
+    const uint32_t rank = cluster_rank();
+    const bool lead = (rank == 0);
+    const int Mt2 = (p.M + 2 * BM - 1) / (2 * BM), Nt = (p.N + BN - 1) / BN;
+    const int ntiles = Mt2 * Nt;
+    const int cid = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
+    const int total = p.kblocks;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 2);
+            mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
+            mbar_init(&tempty[b], 8);  // 4 epilogue warps in each CTA
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(2 * BN)
+    if (warp == 1) {  // one warp of each CTA allocates the pair's tensor memory together
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(PAIR_TMEM_COLS)
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
     fence_before();
     cluster_sync();
@@ -408,47 +441,30 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 0) {
         if (lane == 0) {
             int it = 0;
-            for (int pt = cid; pt < npairs && ok; pt += ncl) {
-                const int m0 = (2 * (pt % Mp) + rank) * BM, n0 = (pt / Mp) * BN;
+            for (int t = cid; t < ntiles && ok; t += ncl) {
+                const int m0 = (t % Mt2) * 2 * BM + (int)rank * BM, n0 = (t / Mt2) * BN + (int)rank * BNH;
                 for (int kk = 0; kk < total; ++kk, ++it) {
                     const int s = it % STAGES, r = it / STAGES;
                     if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    const uint32_t fb = lead ? smem_u32(&full[s]) : peer_addr(&full[s], 0);
+                    if (lead) mbar_expect_tx(&full[s], 2 * L::STAGE);
                     uint8_t *sa = smem + s * L::STAGE;
-                    if constexpr (FUSED) {
-                        // [A plane 0 | A plane 1 | B plane 0 | B plane 1]
-                        uint8_t *sb = sa + 2 * L::A_BYTES;
-                        mbar_expect_tx(&full[s], L::STAGE);
-                        tma_load_3d(sa, &tmA, &full[s], kk * BK, m0, 0);
-                        tma_load_3d(sa + L::A_BYTES, &tmA, &full[s], kk * BK, m0, 1);
-                        tma_load_3d_mc(sb + rank * HALF_BYTES, &tmB, &full[s], kk * BK, n0 + rank * HALF, 0,
-                                       (uint16_t)3);
-                        tma_load_3d_mc(sb + L::B_BYTES + rank * HALF_BYTES, &tmB, &full[s], kk * BK,
-                                       n0 + rank * HALF, 1, (uint16_t)3);
-                    } else {
-                        const int seg = kk / p.kblocks, kb = kk - seg * p.kblocks;
-                        const int pa = (p.seg_pairs >> (4 * seg + 2)) & 3, pb = (p.seg_pairs >> (4 * seg)) & 3;
-                        uint8_t *sb = sa + L::A_BYTES;
-                        mbar_expect_tx(&full[s], L::A_BYTES + L::B_BYTES);
-                        tma_load_3d(sa, &tmA, &full[s], kb * BK, m0, pa);
-                        tma_load_3d_mc(sb + rank * HALF_BYTES, &tmB, &full[s], kb * BK, n0 + rank * HALF, pb,
-                                       (uint16_t)3);
-                    }
+                    uint8_t *sb = sa + 2 * L::A_PLANE;
+                    // [A plane 0 | A plane 1 | B plane 0 | B plane 1]
+                    tma_load_3d_pair(sa, &tmA, fb, kk * BK, m0, 0);
+                    tma_load_3d_pair(sa + L::A_PLANE, &tmA, fb, kk * BK, m0, 1);
+                    tma_load_3d_pair(sb, &tmB, fb, kk * BK, n0, 0);
+                    tma_load_3d_pair(sb + L::B_PLANE, &tmB, fb, kk * BK, n0, 1);
                     issued = it + 1;
                 }
             }
-            // wait until both CTAs have released the last round of every stage, so
-            // that no commit from the peer is still on its way to this CTA
-            if (ok) {
-                for (int it2 = issued > STAGES ? issued - STAGES : 0; it2 < issued; ++it2)
-                    if (!mbar_wait(&empty[it2 % STAGES], (it2 / STAGES) & 1, abort_flag)) { ok = false; break; }
-            }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lead && lane == 0) {
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                   ((uint32_t)(BM >> 4) << 24);
+                                   ((uint32_t)((2 * BM) >> 4) << 24);
             int it = 0, tl = 0;
-            for (int pt = cid; pt < npairs && ok; pt += ncl, ++tl) {
+            for (int t = cid; t < ntiles && ok; t += ncl, ++tl) {
                 const int b = tl & 1, u = tl >> 1;
                 if (!mbar_wait(&tempty[b], (u & 1) ^ 1, abort_flag)) { ok = false; break; }
                 fence_after();
@@ -457,44 +473,39 @@ __global__ void __launch_bounds__(192, 1)
                     const int s = it % STAGES, r = it / STAGES;
                     if (!mbar_wait(&full[s], r & 1, abort_flag)) { ok = false; break; }
                     fence_after();
-                    const uint32_t sa = smem_u32(smem + s * L::STAGE);
-                    if constexpr (FUSED) {
-                        const uint32_t sa1 = sa + L::A_BYTES, sb0 = sa + 2 * L::A_BYTES, sb1 = sb0 + L::B_BYTES;
+                    const uint32_t sa0 = smem_u32(smem + s * L::STAGE), sa1 = sa0 + L::A_PLANE;
+                    const uint32_t sb0 = sa0 + 2 * L::A_PLANE, sb1 = sb0 + L::B_PLANE;
 #pragma unroll
-                        for (int k4 = 0; k4 < BK / 16; ++k4)
-                            mma_bf16(acc, sw128_desc(sa + k4 * 32), sw128_desc(sb0 + k4 * 32), idesc,
-                                     (kk > 0 || k4 > 0) ? 1u : 0u);
+                    for (int k4 = 0; k4 < BK / 16; ++k4)
+                        mma_bf16_pair(acc, sw128_desc(sa0 + k4 * 32), sw128_desc(sb0 + k4 * 32), idesc,
+                                      (kk > 0 || k4 > 0) ? 1u : 0u);
 #pragma unroll
-                        for (int k4 = 0; k4 < BK / 16; ++k4)
-                            mma_bf16(acc, sw128_desc(sa + k4 * 32), sw128_desc(sb1 + k4 * 32), idesc, 1u);
+                    for (int k4 = 0; k4 < BK / 16; ++k4)
+                        mma_bf16_pair(acc, sw128_desc(sa0 + k4 * 32), sw128_desc(sb1 + k4 * 32), idesc, 1u);
 #pragma unroll
-                        for (int k4 = 0; k4 < BK / 16; ++k4)
-                            mma_bf16(acc, sw128_desc(sa1 + k4 * 32), sw128_desc(sb0 + k4 * 32), idesc, 1u);
-                    } else {
-                        const uint32_t sb = sa + L::A_BYTES;
-#pragma unroll
-                        for (int k4 = 0; k4 < BK / 16; ++k4)
-                            mma_bf16(acc, sw128_desc(sa + k4 * 32), sw128_desc(sb + k4 * 32), idesc,
-                                     (kk > 0 || k4 > 0) ? 1u : 0u);
-                    }
-                    mma_commit_mc(&empty[s], (uint16_t)3);
+                    for (int k4 = 0; k4 < BK / 16; ++k4)
+                        mma_bf16_pair(acc, sw128_desc(sa1 + k4 * 32), sw128_desc(sb0 + k4 * 32), idesc, 1u);
+                    mma_commit_pair(smem_u32(&empty[s]));
+                    mma_commit_pair(peer_addr(&empty[s], 1));
                 }
                 if (!ok) break;
-                mma_commit(&tfull[b]);
+                mma_commit_pair(smem_u32(&tfull[b]));
+                mma_commit_pair(peer_addr(&tfull[b], 1));
             }
             if (!ok) {
-                mma_commit(&tfull[0]);
+                // let the MMAs already issued drain before the tensor memory is freed
+                mma_commit_pair(smem_u32(&tfull[0]));
                 mbar_wait(&tfull[0], 0, abort_flag, true);
             }
         }
     } else {
-        const int q = warp & 3;
+        const int q = warp & 3;  // TMEM lane quarter this warp may access
         int tl = 0;
-        for (int pt = cid; pt < npairs; pt += ncl, ++tl) {
+        for (int t = cid; t < ntiles; t += ncl, ++tl) {
             const int b = tl & 1, u = tl >> 1;
             if (!mbar_wait(&tfull[b], u & 1, abort_flag)) { ok = false; break; }
             fence_after();
-            const int m0 = (2 * (pt % Mp) + rank) * BM, n0 = (pt / Mp) * BN;
+            const int m0 = (t % Mt2) * 2 * BM + (int)rank * BM, n0 = (t / Mt2) * BN;
             const int row = m0 + 32 * q + lane;
 #pragma unroll 1
             for (int c = 0; c < BN; c += 32) {
@@ -504,7 +515,7 @@ __global__ void __launch_bounds__(192, 1)
             }
             fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
+            if (lane == 0) mbar_arrive_cluster(lead ? smem_u32(&tempty[b]) : peer_addr(&tempty[b], 0));
         }
     }
     if (!ok) {
@@ -512,15 +523,17 @@ __global__ void __launch_bounds__(192, 1)
         if (p.flags) atomicOr(p.flags, FLAG_TIMEOUT);
     }
     __syncwarp();
-    if (warp == 0 && lane == 0 && *abort_flag) {
+    // after a failure, the even CTA waits (bounded) for the copies in flight of both CTAs
+    if (lead && warp == 0 && lane == 0 && *abort_flag) {
         for (int it = issued > STAGES ? issued - STAGES : 0; it < issued; ++it)
             mbar_wait(&full[it % STAGES], (it / STAGES) & 1, abort_flag, true);
     }
     fence_before();
-    __syncthreads();
+    cluster_sync();
     if (warp == 1) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PAIR_TMEM_COLS)
+                     : "memory");
     }
     cluster_sync();
 }
@@ -575,18 +588,49 @@ uint32_t tc_seg_pairs(int nsplit, int *nseg) {
 void tc_init_attrs() {
     set_attr<256, 4>();
     set_attr<128, 6>();
-    cudaFuncSetAttribute(k_tc_gemm_mc<256, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         McLayout<256, 4, false>::TOTAL);
-    cudaFuncSetAttribute(k_tc_gemm_mc<256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         McLayout<256, 2, true>::TOTAL);
+    cudaFuncSetAttribute(k_tc_gemm_pair<256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         PairLayout<256, 3>::TOTAL);
+    cudaFuncSetAttribute(k_tc_gemm_pair<192, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         PairLayout<192, 4>::TOTAL);
 }
 
-// 0: one CTA per tile; 1: two-CTA clusters sharing B tiles (wide tiles only).
-int g_tc_cluster_mode = 1;
-// Cluster kernel with both split planes per stage (two-plane products only).
-int g_tc_fused = 1;
+// Two-SM pair kernel for wide two-plane products (APF_GEMM_PAIR=0: one-CTA tiles only).
+static bool pair_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("APF_GEMM_PAIR");  // tuning knob; default on
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
 
 int tc_init() { return ensure_encode() ? APF_OK : APF_ECUDA; }
+
+// How many two-CTA clusters of the pair kernel can be resident at once (the
+// SMs of a pair must share a GPC, so this can be below half the SM count).
+static int max_pair_clusters() {
+    static int v = -1;
+    if (v < 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2);
+        cfg.blockDim = dim3(192);
+        cfg.dynamicSmemBytes = PairLayout<256, 3>::TOTAL;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_tc_gemm_pair<256, 3>, &cfg) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 1 << 20;  // unknown: bounded by the SM count below
+        }
+        v = n;
+    }
+    return v;
+}
 
 int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M, int N, int n_cplx, float alpha,
             float beta, float *out_re, float *out_im, long long ldo, const float *in_re, const float *in_im,
@@ -644,21 +688,24 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
     }
     constexpr int smem_wide = Layout<256, 4>::TOTAL, smem_narrow = Layout<128, 6>::TOTAL;
     const int mt = (M + BM - 1) / BM;
-    if (wide && g_tc_cluster_mode == 1 && mt >= 2) {
+    // Pair tiles (256 x BN over two SMs) for wide two-plane products; the tile
+    // width BN in {256, 192} that fills the waves of pair slots best.
+    const int pair_slots = std::max(1, std::min(max_pair_clusters(), (num_sms - reserve) / 2));
+    if (pair_enabled() && nsplit == 2 && mt >= 2 && N >= 256 && pair_slots >= 1) {
+        auto pair_util = [&](int bn) {
+            long long t = (long long)((M + 2 * BM - 1) / (2 * BM)) * ((N + bn - 1) / bn);
+            long long waves = (t + pair_slots - 1) / pair_slots;
+            return (double)t / (double)(waves * pair_slots);
+        };
+        const int pbn = pair_util(192) > 1.1 * pair_util(256) ? 192 : 256;
         CUtensorMap mbh;
-        if (!make_map(&mbh, B, 128)) return set_err(c, APF_ECUDA, "tensor map encode failed (half B)");
-        long long npairs = (long long)((mt + 1) / 2) * ((N + 255) / 256);
-        long long ncl = std::min<long long>(npairs, (num_sms - reserve) / 2);
+        if (!make_map(&mbh, B, pbn / 2)) return set_err(c, APF_ECUDA, "tensor map encode failed (half B)");
+        long long ntp = (long long)((M + 2 * BM - 1) / (2 * BM)) * ((N + pbn - 1) / pbn);
+        long long ncl = std::min<long long>(ntp, pair_slots);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(2 * ncl));
         cfg.blockDim = dim3(192);
-        static int fused_env = -1;
-        if (fused_env < 0) {
-            const char *e = getenv("APF_GEMM_FUSED");  // tuning knob; default on
-            fused_env = (e && e[0] == '0') ? 0 : 1;
-        }
-        const bool fused = (nsplit == 2) && g_tc_fused && fused_env;
-        cfg.dynamicSmemBytes = fused ? McLayout<256, 2, true>::TOTAL : McLayout<256, 4, false>::TOTAL;
+        cfg.dynamicSmemBytes = pbn == 256 ? PairLayout<256, 3>::TOTAL : PairLayout<192, 4>::TOTAL;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -667,9 +714,9 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaError_t e = fused ? cudaLaunchKernelEx(&cfg, k_tc_gemm_mc<256, 2, true>, ma, mbh, p)
-                              : cudaLaunchKernelEx(&cfg, k_tc_gemm_mc<256, 4, false>, ma, mbh, p);
-        if (e != cudaSuccess) return check_cuda(c, e, "cluster GEMM launch");
+        cudaError_t e = pbn == 256 ? cudaLaunchKernelEx(&cfg, k_tc_gemm_pair<256, 3>, ma, mbh, p)
+                                   : cudaLaunchKernelEx(&cfg, k_tc_gemm_pair<192, 4>, ma, mbh, p);
+        if (e != cudaSuccess) return check_cuda(c, e, "pair GEMM launch");
         c->launches++;
     } else if (wide) {
         APF_LAUNCH(c, (k_tc_gemm<256, 4>), grid, 192, smem_wide, s, ma, mb, p);

@@ -34,8 +34,9 @@ def gemm(m, n, k, nsplit=2, reps=3):
     Ar, Ai, Br, Bi = A.real.contiguous(), A.imag.contiguous(), B.real.contiguous(), B.imag.contiguous()
     Cr = torch.empty(m, n, device="cuda")
     Ci = torch.empty(m, n, device="cuda")
-    ts = []
+    ts, tg = [], []
     for _ in range(reps):
+        s.set_profiling(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         rc = L.apf_debug_cgemm(s._h, m, n, k, Ar.data_ptr(), Ai.data_ptr(), Br.data_ptr(), Bi.data_ptr(),
@@ -45,8 +46,13 @@ def gemm(m, n, k, nsplit=2, reps=3):
         if rc:
             raise apf.APFError(rc, L.apf_last_error(s._h).decode())
         ts.append(e0.elapsed_time(e1))
+        tg.append(s.profile()["gemm_ms"])
+    s.set_profiling(False)
+    planes = {1: 1, 2: 3, 3: 6}[nsplit]
+    g_ms = min(tg)
     print(f"gemm {m}x{n}x{k} nsplit {nsplit}: {min(ts):.3f} ms incl. operand packing "
-          f"({8.0 * m * n * k / (min(ts) * 1e-3) / 1e12:.1f} complex TFLOP/s)")
+          f"({8.0 * m * n * k / (min(ts) * 1e-3) / 1e12:.1f} complex TFLOP/s); GEMM launch alone {1000 * g_ms:.1f} us "
+          f"({8.0 * m * n * k * planes / (g_ms * 1e-3) / 1e12:.1f} bf16 TFLOP/s on the tensor pipe)")
 
 
 def inv(n, leaf=128, reps=3):

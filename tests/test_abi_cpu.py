@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version(lib):
-    assert lib.apf_version() >> 16 == 1
+    assert lib.apf_version() >> 16 == 2
 
 
 def test_create_without_device_fails_cleanly(lib):
@@ -53,6 +53,10 @@ def test_create_without_device_fails_cleanly(lib):
 def test_create_rejects_bad_precision(lib):
     h = ctypes.c_void_p()
     assert lib.apf_create(ctypes.byref(h), 0, 77) == apf.APF_EINVAL
+    # the precision enum: 0 float64, 1 TF32 (reserved, not built), 2 bf16x3
+    assert (apf.APF_FP64, apf.APF_MIXED_TF32, apf.APF_MIXED_BF16X3) == (0, 1, 2)
+    assert lib.apf_create(ctypes.byref(h), 0, apf.APF_MIXED_TF32) == apf.APF_EINVAL
+    assert b"TF32" in lib.apf_last_error(None)
 
 
 def test_null_context_calls(lib):
@@ -62,7 +66,7 @@ def test_null_context_calls(lib):
 
 
 def test_new_entry_points_reject_null_context(lib):
-    assert lib.apf_set_ridges(None, None, 0, 1, 4.0, 1.0, -1, 1, 2.25, 1.0, None) == apf.APF_EINVAL
+    assert lib.apf_set_ridges(None, None, 0, 1, 4.0, 1.0, -1, 1, 2.25, 1.0, None, None) == apf.APF_EINVAL
     assert lib.apf_ridge_grad(None, None, None, None) == apf.APF_EINVAL
     assert lib.apf_reflection(None, None, 0, None, None) == apf.APF_EINVAL
     assert lib.apf_reverse_S(None, None, None) == apf.APF_EINVAL

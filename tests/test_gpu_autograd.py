@@ -41,6 +41,84 @@ def test_autograd_backward_equals_builtin_gradient(env, prec, tol):
     assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) <= tol
 
 
+ORDERS = [-2, -1, 0, 1, 2]
+
+
+@pytest.mark.parametrize("prec,tol_s,tol_g", [("fp64", 1e-10, 1e-10), ("mixed", 1e-6, 1e-5)])
+@pytest.mark.parametrize("seed", [0, 3, 9])
+def test_autograd_matches_oracle(env, prec, tol_s, tol_g, seed):
+    """S(eps) -> Eq. 5 loss in torch -> .backward() against the oracle's S, f
+    and its conventional-adjoint gradient (Eq. S1) on the 64 x 100 grid: the
+    whole autograd chain (forward solve, Gamma = conj(dL/dS)/2, the library's
+    adjoint contraction) closed against the independent CPU reference."""
+    torch, apf, AG = env
+    w = W.TINY
+    eps = w.eps_slab(seed)
+    sol, f_ref, _, g_ref = O.f_and_grad(O.problem_from_workload(w, eps), "splitter", ORDERS, 0.18)
+    s = apf.solver_for_workload(w, eps, precision=prec)
+    mi, mo = s.channels()
+    assert list(mi) == list(sol.pb.inputs()) and list(mo) == list(sol.pb.outputs())
+    x = torch.tensor(eps, device="cuda", requires_grad=True)
+    S = AG.scattering(x, s, w.eps_sub, w.eps_clad, w.j0)
+    loss = AG.splitter_loss(S, AG.relative_order_mask(mi, mo, ORDERS, device="cuda"), 0.18)
+    loss.backward()
+    S_h = S.detach().cpu().numpy()
+    g = x.grad.cpu().numpy()
+    assert np.linalg.norm(S_h - sol.S) / np.linalg.norm(sol.S) <= tol_s
+    assert np.max(np.abs(S_h - sol.S)) <= tol_s * np.max(np.abs(sol.S))
+    assert abs(loss.item() - f_ref) <= max(tol_s, 1e-12) * 10 * abs(f_ref)
+    assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) <= tol_g
+    assert np.max(np.abs(g - g_ref)) <= tol_g * np.max(np.abs(g_ref))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_ridge_autograd_matches_oracle(env, prec, tol):
+    """The ridge wrapper (edges -> slab -> S -> Eq. 5 loss, backward to the
+    edges) against the oracle: its pixel gradient pushed through the oracle's
+    edge Jacobian (oracle.grad_edges) on the 64 x 100 grid."""
+    torch, apf, AG = env
+    w = W.TINY
+    edges = W.ridge_edges(w.nx, W.ridge_count(w), 4, mirror=True)
+    eps_r, eps_b = 13.69, 1.0
+    eps = O.eps_from_edges(w.nx, w.h, edges, True, eps_r, eps_b)
+    _, f_ref, _, g_pix = O.f_and_grad(O.problem_from_workload(w, eps), "splitter", ORDERS, 0.18)
+    g_ref = O.grad_edges(g_pix, w.nx, edges, True, eps_r, eps_b)
+    s = apf.Solver(0, prec)
+    s.set_grid(w.nx, w.ny, w.npml, w.npml, w.lambda_px)
+    s.set_ridges(edges, w.h, eps_r, eps_b, w.eps_sub, w.eps_clad, mirror=True, j0=w.j0)
+    s.set_channels(None, None)
+    mi, mo = s.channels()
+    t = torch.tensor(edges, device="cuda", requires_grad=True)
+    S = AG.ridge_scattering(t, s, w.h, eps_r, eps_b, w.eps_sub, w.eps_clad, mirror=True, j0=w.j0)
+    loss = AG.splitter_loss(S, AG.relative_order_mask(mi, mo, ORDERS, device="cuda"), 0.18)
+    loss.backward()
+    g = t.grad.cpu().numpy()
+    assert abs(loss.item() - f_ref) <= 1e-8 * abs(f_ref)
+    assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) <= tol
+
+
+def test_set_eps_reads_device_input_in_stream_order(env):
+    """eps written by torch ops queued on a side stream behind a long matmul,
+    then set_eps with no host synchronization: the library must read the
+    finished values (in order on torch's current stream), so S matches the
+    oracle's S of the intended eps."""
+    torch, apf, AG = env
+    w = W.TINY
+    eps = w.eps_slab(2)
+    sol = O.solve_S(O.problem_from_workload(w, eps))
+    s = apf.solver_for_workload(w, np.full_like(eps, 1.5), precision="fp64")
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        a = torch.randn(4096, 4096, device="cuda", dtype=torch.float64)
+        busy = (a @ a).sum() * 0.0  # keeps the side stream busy for a while
+        x = torch.full(eps.shape, 7.0, dtype=torch.float64, device="cuda")
+        x.copy_(torch.as_tensor(eps, device="cuda") + busy)
+        s.set_eps(x, w.eps_sub, w.eps_clad, j0=w.j0)
+        S = s.solve_S()
+    assert np.linalg.norm(S - sol.S) / np.linalg.norm(sol.S) <= 1e-10
+
+
 def test_gradcheck_tiny(env):
     torch, apf, AG = env
     w, eps = small()

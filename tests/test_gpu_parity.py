@@ -2,7 +2,10 @@
 
 Tolerances (rel-Frobenius over all of S and all slab pixels of df/deps):
 float64 mode 1e-10 on S and on the gradient; mixed mode 1e-6 on S and 1e-5
-on the gradient.
+on the gradient.  Beside the norm, every element is checked: the largest
+absolute difference must stay within the same tolerance times the largest
+reference entry, so one wrong small entry (a near-grazing order, one pixel)
+cannot hide inside the norm.
 """
 import os
 
@@ -33,6 +36,15 @@ def apf():
     return A
 
 
+def close(got, ref, tol):
+    """rel-Frobenius and element-wise max-abs agreement within tol."""
+    got, ref = np.asarray(got), np.asarray(ref)
+    e_fro = rel(got, ref)
+    e_max = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    assert e_fro <= tol and e_max <= tol, (e_fro, e_max, tol)
+    return e_fro
+
+
 def make_solver(apf, pb, precision):
     s = apf.Solver(device=0, precision=precision)
     s.set_grid(pb.nx, pb.ny, pb.npml_bot, pb.npml_top, pb.lambda_px, R0=pb.R0, power=pb.power)
@@ -44,14 +56,9 @@ def make_solver(apf, pb, precision):
 PRECS = ["fp64", "mixed"]
 
 
-def _skip_if_unbuilt(apf, prec):
-    return None
-
-
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_tiny_S_and_grad(apf, prec, seed):
-    _skip_if_unbuilt(apf, prec)
     w = W.TINY
     pb = O.problem_from_workload(w, w.eps_slab(seed))
     orders = [-2, -1, 0, 1, 2]
@@ -62,21 +69,21 @@ def test_tiny_S_and_grad(apf, prec, seed):
     S, f, g = s.solve_S_grad("splitter", orders, 0.18)
     ts, tg = TOL[prec]
     print(f"parity tiny seed {seed} {prec}: err S {rel(S, sol.S):.2e}, err grad {rel(g, g_ref):.2e}")
-    assert rel(S, sol.S) <= ts
-    assert rel(g, g_ref) <= tg
+    close(S, sol.S, ts)
+    close(g, g_ref, tg)
     assert abs(f - f_ref) <= ts * abs(f_ref) * 10
 
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_tiny_power_objective(apf, prec):
-    _skip_if_unbuilt(apf, prec)
     w = W.TINY
     pb = O.problem_from_workload(w, w.eps_slab(3))
     sol, f_ref, _, g_ref = O.f_and_grad(pb, "power", [0], 0.0)
     s = make_solver(apf, pb, prec)
     S, f, g = s.solve_S_grad("power", [0])
     ts, tg = TOL[prec]
-    assert rel(S, sol.S) <= ts and rel(g, g_ref) <= tg
+    close(S, sol.S, ts)
+    close(g, g_ref, tg)
 
 
 # Ragged and edge cases: one leaf (nx=32), several leaves (nx=128), a single
@@ -93,7 +100,6 @@ EDGE = [
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("case", range(len(EDGE)))
 def test_edge_cases(apf, prec, case):
-    _skip_if_unbuilt(apf, prec)
     c = EDGE[case]
     eps = W.iid_eps(c["h"], c["nx"], 100 + case, 1.0, 3.0)
     j0 = c["j0"] if c["j0"] >= 0 else c["nb"] + (c["ny"] - c["nb"] - c["nt"] - c["h"]) // 2
@@ -105,15 +111,14 @@ def test_edge_cases(apf, prec, case):
     s = make_solver(apf, pb, prec)
     S, f, g = s.solve_S_grad("splitter", [-1, 0, 1], 0.3)
     ts, tg = TOL[prec]
-    assert rel(S, sol.S) <= ts, rel(S, sol.S)
-    assert rel(g, g_ref) <= tg, rel(g, g_ref)
+    close(S, sol.S, ts)
+    close(g, g_ref, tg)
 
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_mid_against_golden(apf, prec):
     """1024 x 240, 103 x 103 channels, against oracle values written by
     tests/golden/make_golden.py."""
-    _skip_if_unbuilt(apf, prec)
     ref = np.load(os.path.join(HERE, "golden", "mid_1024x240_seed0.npz"))
     w = W.MID
     eps = w.eps_slab(0)
@@ -123,15 +128,14 @@ def test_mid_against_golden(apf, prec):
     S, f, g = s.solve_S_grad("splitter", [-2, -1, 0, 1, 2], 0.18)
     ts, tg = TOL[prec]
     print(f"parity mid {prec}: err S {rel(S, ref['S']):.2e}, err grad {rel(g, ref['grad']):.2e}")
-    assert rel(S, ref["S"]) <= ts, rel(S, ref["S"])
-    assert rel(g, ref["grad"]) <= tg, rel(g, ref["grad"])
+    close(S, ref["S"], ts)
+    close(g, ref["grad"], tg)
 
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_grad_from_gamma_and_device_buffers(apf, prec):
     """Caller-supplied Gamma after solve_S equals the built-in objective path;
     device (torch) buffers give the same result as host buffers."""
-    _skip_if_unbuilt(apf, prec)
     import torch
     w = W.TINY
     pb = O.problem_from_workload(w, w.eps_slab(4))

@@ -75,3 +75,49 @@ def test_noalloc_rejects_sizes_beyond_the_limit(lib):
                                w.eps_sub, w.eps_clad, None, 0, None, 0, out.ctypes.data, None)
     assert rc == apf.APF_EINVAL
     assert b"nx" in L.apf_last_error(None)
+
+
+def test_noalloc_at_its_size_limit_on_a_side_stream(lib):
+    """The tightest fit of the scratch array: nx = 64, h = 16 and 63 + 63
+    explicit channel orders (the most that nx = 64 admits: order -32 never
+    propagates when order 0 does), with device buffers on a non-default
+    stream, twice in a row, against the context-based solve."""
+    apf, L = lib
+    import torch
+    nx, ny, npml, h = 64, 80, 20, 16
+    lam = 2.0 * np.pi / (2.0 * np.sqrt(0.9999))  # k^2/4 just below 1: orders -31..31 propagate
+    orders = list(range(-31, 32))
+    side = torch.cuda.Stream()
+    for seed in (5, 6):
+        eps = np.ascontiguousarray(W.iid_eps(h, nx, seed, 1.0, 2.0))
+        s = apf.Solver(0, "fp64")
+        s.set_grid(nx, ny, npml, npml, lam)
+        s.set_eps(eps, 1.0, 1.0)
+        s.set_channels(orders, orders)
+        ref = s.solve_S()
+        s.close()
+        oi = (ctypes.c_int * len(orders))(*orders)
+        with torch.cuda.stream(side):
+            eps_d = torch.tensor(eps, device="cuda")
+            S_d = torch.full((len(orders), len(orders)), complex("nan+nanj"), dtype=torch.complex128, device="cuda")
+            rc = L.apf_solve_S_noalloc(nx, ny, npml, npml, lam, None, eps_d.data_ptr(), -1, h, 1.0, 1.0,
+                                       oi, len(orders), oi, len(orders), S_d.data_ptr(),
+                                       ctypes.c_void_p(side.cuda_stream))
+        assert rc == 0, L.apf_last_error(None)
+        got = S_d.cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL_FP64, seed
+
+
+@pytest.mark.parametrize("what", ["h", "channels"])
+def test_noalloc_rejects_just_over_the_limit(lib, what):
+    apf, L = lib
+    nx, ny, npml = 64, 100, 20
+    h = 17 if what == "h" else 16
+    eps = np.ascontiguousarray(np.full((h, nx), 1.5))
+    n = 65 if what == "channels" else 4
+    orders = (ctypes.c_int * n)(*range(n))
+    out = np.empty((n, n), np.complex128)
+    rc = L.apf_solve_S_noalloc(nx, ny, npml, npml, 16.0, None, eps.ctypes.data, -1, h, 2.25, 1.0,
+                               orders, n, orders, n, out.ctypes.data, None)
+    assert rc == apf.APF_EINVAL
+    assert (b"h must be" if what == "h" else b"channels") in L.apf_last_error(None)
