@@ -41,6 +41,12 @@ TARGET = 0.18
 EPS_RIDGE, EPS_BG = 13.69, 1.0  # amorphous-silicon ridges in air (Sec. 3: n = 3.70)
 WL = {"mid": W.MID, "large": W.LARGE, "xlarge": W.XLARGE, "tiny": W.TINY}
 
+# DRAM traffic of the tensor-core GEMM per bf16 tensor flop, from one ncu
+# capture of the field-sweep product (dram__bytes_read.sum + dram__bytes_write.sum
+# divided by 8 m n k x 3 plane products of that launch); a launch's traffic is
+# this times its flops.  None until a capture of the current kernel exists.
+GEMM_CAPTURE = {"bytes_per_hw_flop": None, "profile": "none"}
+
 
 def args_parse():
     p = argparse.ArgumentParser()
@@ -50,7 +56,9 @@ def args_parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="large", choices=sorted(WL))
     p.add_argument("--fp64-steps", type=int, default=1, help="timed float64 steps for the comparison (0 = skip)")
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--recompute-rows", type=int, default=4,
+                   help="segment rows for the timed recompute-instead-of-store variant (0 = skip)")
+    p.add_argument("--opt-iters", type=int, default=3, help="timed optimisation iterations on one design (0 = skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--solves", type=int, default=4, help="oracle solves per CPU sample")
     p.add_argument("--refine-tol", type=float, default=1e-7,
@@ -230,6 +238,38 @@ def run_reference(a, w):
     print(json.dumps(line), flush=True)
 
 
+def alg_flops(w, nin, nout):
+    """Algorithmic real flops of one S + grad f evaluation (8 per complex
+    multiply-add): symmetric recursive inversion of the h slab blocks
+    (h (16/3) n^3), the first field sweep (8 n^2 [(h-1) n_in + h (n_in + n_out)])
+    and the adjoint contraction (8 h n n_in n_out)."""
+    n, h = float(w.nx), float(w.h)
+    return h * 16.0 / 3.0 * n ** 3 + 8.0 * n * n * ((h - 1) * nin + h * (nin + nout)) + 8.0 * h * n * nin * nout
+
+
+def fp64_peak(local):
+    """Measured float64 matrix-multiply rate of this GPU (cuBLAS DGEMM through
+    torch, 8192^3, best of 3): the denominator for the float64 path."""
+    import torch
+    dev = torch.device("cuda", local)
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / best / 1e12
+
+
 def main():
     a = args_parse()
     w = WL[a.workload]
@@ -237,6 +277,8 @@ def main():
     if a.impl == "reference":
         run_reference(a, w)
         return
+    import threading
+
     import torch
     import torch.distributed as dist
 
@@ -252,10 +294,10 @@ def main():
     seeds = replicas.replica_seeds(rank, B, nseeds)
     if ridges:
         nr = W.ridge_count(w)
-        eps_host = [[W.ridge_edges(w.nx, nr, sd, mirror=True) for sd in row] for row in seeds]
+        x_host = [[W.ridge_edges(w.nx, nr, sd, mirror=True) for sd in row] for row in seeds]
     else:
-        eps_host = [[w.eps_slab(sd) for sd in row] for row in seeds]
-    eps_dev = [[torch.tensor(e, device=dev) for e in row] for row in eps_host]
+        x_host = [[w.eps_slab(sd) for sd in row] for row in seeds]
+    x_dev = [[torch.tensor(e, device=dev) for e in row] for row in x_host]
 
     def set_design(sv, x):
         """x: a permittivity slab, or ridge edge positions with --design ridges."""
@@ -264,58 +306,64 @@ def main():
         else:
             sv.set_eps(x, w.eps_sub, w.eps_clad, j0=w.j0)
 
-    solvers = []
-    for b in range(B):
-        sv = apf.Solver(device=local, precision="mixed")
+    def new_solver(prec, x):
+        sv = apf.Solver(device=local, precision=prec)
         sv.set_grid(w.nx, w.ny, w.npml, w.npml, w.lambda_px)
-        set_design(sv, eps_host[b][0])
+        set_design(sv, x)
         sv.set_channels(None, None)
-        solvers.append(sv)
-    if a.refine_tol is not None:
-        for sv in solvers:
+        if prec == "mixed":
             sv.set_refinement(a.refine_tol, 40)
+        return sv
+
+    solvers = [new_solver("mixed", x_host[b][0]) for b in range(B)]
     s = solvers[0]
     m_in, m_out = s.channels()
+    nin, nout = len(m_in), len(m_out)
     streams = [torch.cuda.Stream(device=dev) for _ in range(B)]
-    S_d = [torch.empty((len(m_out), len(m_in)), dtype=torch.complex128, device=dev) for _ in range(B)]
+    S_d = [torch.empty((nout, nin), dtype=torch.complex128, device=dev) for _ in range(B)]
     g_d = [torch.empty((w.h, w.nx), dtype=torch.float64, device=dev) for _ in range(B)]
-    ge_d = [torch.empty(len(eps_host[0][0]) if ridges else 1, dtype=torch.float64, device=dev) for _ in range(B)]
+    ge_d = [torch.empty(len(x_host[0][0]) if ridges else 1, dtype=torch.float64, device=dev) for _ in range(B)]
     stats_acc = [dict(launches=0, iters=[], fallbacks=0) for _ in range(B)]
 
-    def step(b, i):
+    def step_dev(b, i):
+        """One evaluation with device-resident inputs and outputs."""
         sv = solvers[b]
-        set_design(sv, eps_dev[b][i % nseeds])
-        r = sv.solve_S_grad("splitter", ORDERS, TARGET, out_S=S_d[b], out_grad=g_d[b])
+        set_design(sv, x_dev[b][i % nseeds])
+        sv.solve_S_grad("splitter", ORDERS, TARGET, out_S=S_d[b], out_grad=g_d[b])
         if ridges:
             sv.ridge_grad(g_d[b], out=ge_d[b])
-        return r
 
-    def worker(b, nsteps, start_ev, end_evs, record):
-        with torch.cuda.stream(streams[b]):
-            if start_ev is not None:
-                streams[b].wait_event(start_ev)
-            for i in range(nsteps):
-                step(b, i)
-                if record:
-                    st = solvers[b].stats()
-                    stats_acc[b]["launches"] += st["kernel_launches"]
-                    stats_acc[b]["iters"].append(st["refine_iters"])
-                    stats_acc[b]["fallbacks"] += st["leaf_fallbacks"]
-            if end_evs is not None:
-                end_evs[b].record(streams[b])
-
-    import threading
+    def step_host(b, i):
+        """One evaluation through the public API with host buffers: the design
+        goes host -> device, S, f and the gradient come back to the host."""
+        sv = solvers[b]
+        set_design(sv, x_host[b][i % nseeds])
+        if ridges:
+            sv.solve_S_grad("splitter", ORDERS, TARGET, out_grad=g_d[b])
+            sv.ridge_grad(g_d[b])
+        else:
+            sv.solve_S_grad("splitter", ORDERS, TARGET)
 
     errors = []
 
-    def guarded(*args):
-        try:
-            worker(*args)
-        except BaseException as e:  # re-raised on the main thread: a failed step fails the bench
-            errors.append(e)
-
-    def run_all(nsteps, start_ev=None, end_evs=None, record=False):
-        ths = [threading.Thread(target=guarded, args=(b, nsteps, start_ev, end_evs, record)) for b in range(B)]
+    def run_all(fn, nsteps, start_ev=None, end_evs=None, record=False, nb=B):
+        def worker(b):
+            try:
+                with torch.cuda.stream(streams[b]):
+                    if start_ev is not None:
+                        streams[b].wait_event(start_ev)
+                    for i in range(nsteps):
+                        fn(b, i)
+                        if record:
+                            st = solvers[b].stats()
+                            stats_acc[b]["launches"] += st["kernel_launches"]
+                            stats_acc[b]["iters"].append(st["refine_iters"])
+                            stats_acc[b]["fallbacks"] += st["leaf_fallbacks"]
+                    if end_evs is not None:
+                        end_evs[b].record(streams[b])
+            except BaseException as e:  # re-raised on the main thread: a failed step fails the bench
+                errors.append(e)
+        ths = [threading.Thread(target=worker, args=(b,)) for b in range(nb)]
         for t in ths:
             t.start()
         for t in ths:
@@ -323,12 +371,9 @@ def main():
         if errors:
             raise errors[0]
 
-    for sv in solvers:
-        sv.set_profiling(True)
-    run_all(a.warmup)
+    # ---- 1. the headline: B designs in flight, inputs resident on the device ----
+    run_all(step_dev, a.warmup)
     torch.cuda.synchronize()
-    for sv in solvers:
-        sv.set_profiling(True)  # reset the counters, keep the captured graphs
     clk = Clocks(local)
     master = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -339,7 +384,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     e0.record(master)
-    run_all(a.steps, e0, ends, record=True)
+    run_all(step_dev, a.steps, e0, ends, record=True)
     for ev in ends:
         master.wait_event(ev)
     e1.record(master)
@@ -347,43 +392,139 @@ def main():
     if ws > 1:
         dist.barrier()
     clocks = clk.stop()
-    profs = [sv.profile() for sv in solvers]
-    prof = {k: sum(p[k] for p in profs) for k in profs[0]}
-    for sv in solvers:
-        sv.set_profiling(False)
     ms = replicas.max_over_ranks(e0.elapsed_time(e1))
     value = replicas.whole_job_throughput(ws, B, a.steps, ms)
     launches = sum(x["launches"] for x in stats_acc)
     iters = stats_acc[0]["iters"]
     st_last = s.stats()
-    eps_host = eps_host[0]
 
-    # end to end through the public API with host buffers (H2D eps, D2H S/grad/f)
-    e2e_t = []
-    for i in range(a.e2e_steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        set_design(s, eps_host[i % nseeds])
-        if ridges:
-            # host edges in, host S, f and df/d(edges) out; the pixel gradient stays on the device
-            S_h, f_h, _ = s.solve_S_grad("splitter", ORDERS, TARGET, out_grad=g_d[0])
-            ge_h = s.ridge_grad(g_d[0])
-        else:
-            S_h, f_h, g_h = s.solve_S_grad("splitter", ORDERS, TARGET)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_val = ws * 1.0 / statistics.mean(e2e_t) if e2e_t else None
+    # ---- 2. end to end at the same concurrency and step count: host buffers ----
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    run_all(step_host, a.steps)
+    torch.cuda.synchronize()
+    t_e2e = replicas.max_over_ranks(time.perf_counter() - t0)
+    e2e_val = ws * B * a.steps / t_e2e
     if ridges:
-        ne = len(eps_host[0])
+        ne = len(x_host[0][0])
         h2d = ne * 8
-        d2h = len(m_in) * len(m_out) * 16 + ne * 8 + 8
+        d2h = nin * nout * 16 + ne * 8 + 8
     else:
         h2d = w.h * w.nx * 8
-        d2h = len(m_in) * len(m_out) * 16 + w.h * w.nx * 8 + 8
+        d2h = nin * nout * 16 + w.h * w.nx * 8 + 8
 
-    # properties that hold at any size, on the last design solved by solver 0:
-    # reciprocity between the forward (S) and adjoint (reverse S) columns, and
-    # flux conservation with the reflection block (up to the PML's reflection)
+    # ---- 3. one design alone: its rate and the tensor-core GEMM's in-step roofline ----
+    # (a single stream, so every GEMM's CUDA-event interval is that launch alone)
+    s.set_profiling(True)
+    for i in range(2):
+        step_dev(0, i)
+    torch.cuda.synchronize()
+    s.set_profiling(True)  # reset the counters, keep the captured graphs
+    n1 = max(3, a.steps // 2)
+    with torch.cuda.stream(streams[0]):
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(streams[0])
+        for i in range(n1):
+            step_dev(0, i)
+        f1.record(streams[0])
+    torch.cuda.synchronize()
+    ms1 = f0.elapsed_time(f1) / n1
+    prof = s.profile()
+    s.set_profiling(False)
+    single = {"value": 1000.0 / ms1, "unit": "evals/s", "steps": n1, "ms_per_step": ms1,
+              "gemm_ms_per_step": prof["gemm_ms"] / n1, "gemm_launches_per_step": prof["gemm_launches"] / n1}
+
+    # ---- 4. the float64 GPU path, the same design, one design at a time ----
+    fp64 = None
+    if a.fp64_steps > 0:
+        s64 = new_solver("fp64", x_host[0][0])
+        fn64 = lambda: s64.solve_S_grad("splitter", ORDERS, TARGET)  # noqa: E731
+        fn64()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.fp64_steps):
+            S64, f64v, g64 = fn64()
+            if ridges:
+                g64 = s64.ridge_grad(g64)
+        t64 = (time.perf_counter() - t0) / a.fp64_steps
+        set_design(s, x_host[0][0])
+        Sm, fm, gm = s.solve_S_grad("splitter", ORDERS, TARGET)
+        if ridges:
+            gm = s.ridge_grad(gm)
+        pk64 = fp64_peak(local)
+        fl = alg_flops(w, nin, nout)
+        fp64 = {"value": 1.0 / t64, "unit": "evals/s", "steps": a.fp64_steps, "designs": 1,
+                "err_S_mixed_vs_fp64": rel(Sm, S64), "err_grad_mixed_vs_fp64": rel(gm, g64),
+                "speedup_mixed_over_fp64_1_design": single["value"] * t64,
+                "speedup_mixed_B_designs_over_fp64_1_design": value / ws * t64,
+                "fp64_peak_tflops_measured": pk64,
+                "alg_tflops": fl / t64 / 1e12, "frac_of_fp64_peak": fl / t64 / 1e12 / pk64,
+                "note": ("float64 path (SIMT k_zgemm): one design per call, wall clock; fp64 peak = torch float64 "
+                         "8192^3 matmul (cuBLAS) timed in this run")}
+        s64.close()
+
+    # ---- 5. the conventional adjoint method (Eq. S1) on the same elimination, one design ----
+    adj = None
+    if not ridges:
+        set_design(s, x_host[0][0])
+        Sp, fp_, gp = s.solve_S_grad("splitter", ORDERS, TARGET)
+        Sa, fa, ga = s.solve_S_grad_adjoint("splitter", ORDERS, TARGET)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(streams[0]):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(streams[0])
+            for i in range(n1):
+                set_design(s, x_dev[0][i % nseeds])
+                s.solve_S_grad_adjoint("splitter", ORDERS, TARGET, out_S=S_d[0], out_grad=g_d[0])
+            a1.record(streams[0])
+        torch.cuda.synchronize()
+        ms_adj = a0.elapsed_time(a1) / n1
+        adj = {"value": 1000.0 / ms_adj, "unit": "evals/s", "designs": 1,
+               "speedup_apf_over_adjoint": ms_adj / ms1, "err_grad_adjoint_vs_apf": rel(ga, gp),
+               "err_S_adjoint_vs_apf": rel(Sa, Sp),
+               "note": ("forward sweep of n_in columns, S and Gamma, then a second sweep of n_in adjoint "
+                        "columns (sources sum_b Gamma_ba C_b), each refined; the paper's ~150x (Table S1) is "
+                        "for a sparse direct solver on one CPU core, where the adjoint method re-solves per input")}
+
+    # ---- 6. slab Schur blocks recomputed instead of stored, one design ----
+    rec = None
+    if not ridges and a.recompute_rows > 0:
+        sr = new_solver("mixed", x_host[0][0])
+        sr.set_schur_storage(a.recompute_rows)
+        for i in range(2):
+            sr.solve_S_grad("splitter", ORDERS, TARGET, out_S=S_d[0], out_grad=g_d[0])
+        torch.cuda.synchronize()
+        with torch.cuda.stream(streams[0]):
+            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            r0.record(streams[0])
+            for i in range(n1):
+                set_design(sr, x_dev[0][i % nseeds])
+                sr.solve_S_grad("splitter", ORDERS, TARGET, out_S=S_d[0], out_grad=g_d[0])
+            r1.record(streams[0])
+        torch.cuda.synchronize()
+        ms_rec = r0.elapsed_time(r1) / n1
+        rec = {"segment_rows": a.recompute_rows, "value": 1000.0 / ms_rec, "unit": "evals/s", "designs": 1,
+               "workspace_bytes": sr.stats()["workspace_bytes"], "workspace_bytes_stored": st_last["workspace_bytes"],
+               "slowdown_vs_stored": ms_rec / ms1}
+        sr.close()
+
+    # ---- 7. gradient-descent optimisation (Armijo line search, Supplement Sec. 4), one design ----
+    opt = None
+    if not ridges and a.opt_iters > 0:
+        from paper_2306_09257_gb300 import optim
+        _, hist = optim.optimize(s, x_host[0][0], w.eps_sub, w.eps_clad, w.j0, "splitter", ORDERS, TARGET,
+                                 a.opt_iters)
+        opt = {"iterations": len(hist.f) - 1, "evaluations": hist.evals, "seconds": hist.seconds,
+               "iters_per_s": hist.iters_per_second, "f_first": hist.f[0], "f_last": hist.f[-1],
+               "note": "host loop: every trial point is one S + grad evaluation with host buffers"}
+
+    # properties that hold at any size, on one design: reciprocity between the
+    # forward (S) and adjoint (reverse S) columns, and flux conservation with the
+    # reflection block (up to the PML's reflection)
     checks = None
+    set_design(s, x_host[0][0])
     if s.channels()[1].tolist() == sorted(-m for m in s.channels()[1].tolist()):
         S_c = s.solve_S()
         R_c = s.reflection()
@@ -393,93 +534,75 @@ def main():
         qi = {int(m): i for i, m in enumerate(mo_c)}
         T = np.array([[Sr_c[pi[-int(ma)], qi[-int(mb)]] for ma in mi_c] for mb in mo_c])
         flux = (np.abs(S_c) ** 2).sum(0) + (np.abs(R_c) ** 2).sum(0)
-        dev = np.abs(flux - 1.0)
-        checks = {"reciprocity_rel_err": rel(T, S_c), "flux_dev_median": float(np.median(dev)),
-                  "flux_dev_max": float(dev.max()),
+        dv = np.abs(flux - 1.0)
+        checks = {"reciprocity_rel_err": rel(T, S_c), "flux_dev_median": float(np.median(dv)),
+                  "flux_dev_max": float(dv.max()),
                   "note": "mixed path at the bench's refinement tolerance; flux is PML-limited "
                           "(near-grazing orders ~2e-2)"}
 
-    # float64 GPU path on the same workload and the mixed-vs-float64 error
-    fp64 = None
-    if a.fp64_steps > 0:
-        s64 = apf.Solver(device=local, precision="fp64")
-        s64.set_grid(w.nx, w.ny, w.npml, w.npml, w.lambda_px)
-        set_design(s64, eps_host[0])
-        s64.set_channels(None, None)
-        s64.solve_S_grad("splitter", ORDERS, TARGET)  # warm-up
-        t0 = time.perf_counter()
-        for _ in range(a.fp64_steps):
-            S64, f64v, g64 = s64.solve_S_grad("splitter", ORDERS, TARGET)
-            if ridges:
-                g64 = s64.ridge_grad(g64)
-        t64 = (time.perf_counter() - t0) / a.fp64_steps
-        set_design(s, eps_host[0])
-        Sm, fm, gm = s.solve_S_grad("splitter", ORDERS, TARGET)
-        if ridges:
-            gm = s.ridge_grad(gm)
-        fp64 = {"value": 1.0 / t64, "unit": "evals/s", "steps": a.fp64_steps,
-                "err_S_mixed_vs_fp64": rel(Sm, S64), "err_grad_mixed_vs_fp64": rel(gm, g64),
-                "speedup_mixed_over_fp64": value / ws * t64,
-                "note": "float64 path timed one design at a time (single stream)"}
-        s64.close()
-
     pk, src = peaks()
-    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    peak_sus = pk.get("bf16_tflops_sustained", 1700.0)
+    burst = pk.get("bf16_tflops", 1900.0)
     hw_tf = prof["gemm_hw_flops"] / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else 0.0
     alg_tf = prof["gemm_alg_flops"] / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else 0.0
-    gemm_share = prof["gemm_ms"] / (B * ms) if ms > 0 else 0.0
-    agg_tf = prof["gemm_hw_flops"] / (ms / 1e3) / 1e12 if ms > 0 else 0.0
-    roofline = {"bound": "tensor", "achieved": hw_tf, "peak": peak, "unit": "TFLOP/s", "frac": hw_tf / peak,
-                "traffic": None, "kernel": "k_tc_gemm (tcgen05 bf16, fp32 accumulate)",
+    per_launch_flops = prof["gemm_hw_flops"] / max(1, prof["gemm_launches"])
+    traffic = None
+    if GEMM_CAPTURE["bytes_per_hw_flop"] is not None:
+        traffic = GEMM_CAPTURE["bytes_per_hw_flop"] * per_launch_flops
+    roofline = {"bound": "tensor", "achieved": hw_tf, "peak": peak_sus, "unit": "TFLOP/s",
+                "frac": hw_tf / peak_sus, "traffic": traffic,
+                "kernel": "k_tc_gemm_pair / k_tc_gemm (tcgen05 bf16, fp32 accumulate)",
                 "achieved_algorithmic_complex_tflops": alg_tf,
-                "aggregate_tflops_over_step": agg_tf,
-                "note": (f"achieved = bf16 tensor flops (8 m n k per complex product x plane products) / "
-                         f"summed CUDA-event launch time over the timed region; peak = bf16_tflops_sustained "
-                         f"({src}); GEMM time share of step {gemm_share:.2f}")}
-
-    iso = isolated_gemm(apf, local, len(m_in) + len(m_out), w.nx, w.nx)
+                "note": (f"one design alone on one stream ({n1} steps): achieved = bf16 tensor flops (8 m n k per "
+                         f"complex product x plane products) / summed CUDA-event launch time "
+                         f"({prof['gemm_ms'] / n1:.2f} ms of the {ms1:.2f} ms step); peak = bf16_tflops_sustained "
+                         f"({src}, of measured); traffic = DRAM bytes per launch scaled from the ncu capture "
+                         f"{GEMM_CAPTURE['profile']} by the launch's flops")}
+    iso = isolated_gemm(apf, local, nin + nout, w.nx, w.nx)
     if iso:
-        burst = pk.get("bf16_tflops", 1964.9)
         iso_tf = iso["gemm_hw_flops"] / (iso["gemm_ms"] / 1e3) / 1e12
         roofline["isolated"] = {
-            "kernel": f"k_tc_gemm, field-sweep product {len(m_in) + len(m_out)}x{w.nx}x{w.nx} complex, alone",
+            "kernel": f"field-sweep product {nin + nout}x{w.nx}x{w.nx} complex, alone",
             "achieved": iso_tf, "peak": burst, "frac": iso_tf / burst, "unit": "TFLOP/s",
             "us_per_launch": 1000.0 * iso["gemm_ms"],
-            "note": "CUDA events around the one GEMM launch; peak = bf16_tflops (burst), as for a kernel timed alone"}
+            "note": "CUDA events around the one GEMM launch; peak = bf16_tflops (burst, of measured)"}
 
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         if ridges:
             import oracle as O
-            eps_cpu = O.eps_from_edges(w.nx, w.h, eps_host[0], True, EPS_RIDGE, EPS_BG)
+            eps_cpu = O.eps_from_edges(w.nx, w.h, x_host[0][0], True, EPS_RIDGE, EPS_BG)
         else:
-            eps_cpu = eps_host[0]
-        t_eval, t_fac, t_solve, nin = cpu_oracle_sample(w, eps_cpu, a.solves)
+            eps_cpu = x_host[0][0]
+        t_eval, t_fac, t_solve, nin_c = cpu_oracle_sample(w, eps_cpu, a.solves)
         cpu = {"value": 1.0 / t_eval, "unit": "evals/s", "cores": 1, "kind": "oracle",
                "sample": (f"SuperLU factor ({t_fac:.1f} s, serial) + {a.solves} forward and {a.solves} adjoint "
-                          f"solves ({t_solve:.3f} s each), extrapolated to 2*{nin} solves per evaluation")}
+                          f"solves ({t_solve:.3f} s each), extrapolated to 2*{nin_c} solves per evaluation")}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
                 "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "npml": w.npml, "lambda_px": w.lambda_px,
-                           "h": w.h, "channels": [len(m_in), len(m_out)],
-                           "eps": (f"ridges: {len(eps_host[0]) // 2} per half period, mirror symmetric, eps "
-                                   f"{EPS_RIDGE}/{EPS_BG}, gradient to the {len(eps_host[0])} edge positions"
+                           "h": w.h, "channels": [nin, nout],
+                           "eps": (f"ridges: {len(x_host[0][0]) // 2} per half period, mirror symmetric, eps "
+                                   f"{EPS_RIDGE}/{EPS_BG}, gradient to the {len(x_host[0][0])} edge positions"
                                    if ridges else "filtered-threshold, seeded"),
                            "objective": "beam splitter Eq. 5, orders -2..2, t=0.18",
-                           "l2": f"working set {st_last['workspace_bytes'] / 1e9:.1f} GB > 129 MB L2, no flush",
+                           "l2": f"working set {st_last['workspace_bytes'] / 1e9:.1f} GB per design > 129 MB L2, no flush",
                            "refine_iters": iters, "residual": st_last["residual"],
                            "leaf_fallbacks_per_step": sum(x["fallbacks"] for x in stats_acc) / (B * a.steps),
                            "concurrent_designs_per_gpu": B,
                            "parallelism": f"replicas x{ws}, {B} independent designs per GPU"},
-                "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "designs": B, "steps": a.steps,
+                        "note": "same designs in flight and step count as value; wall clock incl. host copies"},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu,
-                "fp64": fp64, "checks": checks, "concurrent_designs": B, "refine_tol": a.refine_tol if a.refine_tol else 1e-10,
+                "single_design": single, "fp64": fp64, "adjoint_method": adj, "schur_recompute": rec,
+                "optimisation": opt,
+                "checks": checks, "concurrent_designs": B, "refine_tol": a.refine_tol,
                 "stages_ms": {k: st_last[k] for k in ("ms_boundary", "ms_eliminate", "ms_fields", "ms_readout",
-                                                       "ms_gradient")},
-                "gemm": {"launches": prof["gemm_launches"], "ms": prof["gemm_ms"]}}
+                                                       "ms_gradient")}}
         print(json.dumps(line), flush=True)
     for sv in solvers:
         sv.close()

@@ -150,6 +150,20 @@ int apf_solve_S(apf_ctx *ctx, double *S, void *stream);
 int apf_solve_S_grad(apf_ctx *ctx, int objective, const double *params, int n_params,
                      double *S, double *f, double *grad_eps, void *stream);
 
+/* The paper's conventional adjoint method (Supplement Sec. 1, Eq. S1), the
+   baseline that APF is measured against (Supplement Table S1), on the same
+   structured elimination: the M_in forward fields A^-1 B_a, S and Gamma =
+   df/dS, then M_in adjoint fields with the sources C_a^adj = sum_b Gamma_ba
+   C_b (known only after Gamma, so a second sweep), and df/deps_k =
+   2 k^2 Re sum_a (A^-1 C_a^adj^T)_k (A^-1 B_a)_k.  Same arguments, results and
+   errors as apf_solve_S_grad (S, f and df/deps agree with it to rounding);
+   in mixed mode each of the two sweeps is refined to the tolerance of
+   apf_set_refinement.  The adjoint fields it leaves are not those
+   apf_grad_from_gamma and apf_reverse_S need (APF_ESTATE until the next
+   apf_solve_S or apf_solve_S_grad). */
+int apf_solve_S_grad_adjoint(apf_ctx *ctx, int objective, const double *params, int n_params,
+                             double *S, double *f, double *grad_eps, void *stream);
+
 /* df/deps = 2 Re sum_ba Gamma_ba dS_ba/deps for a caller-supplied
    Gamma = df/dS (n_out x n_in complex128), using the fields of the last
    solve (Eq. 1 with Eq. 3).  grad_eps: h*nx float64. */
@@ -185,7 +199,7 @@ int apf_reverse_S(apf_ctx *ctx, double *S_rev, void *stream);
 
 /* Ridge metasurface parametrization (paper Sec. 3 and Eq. 5: the design
    variables are the edge positions of the ridges; mirror symmetry maps the
-   free half period onto the other half, Supplement Sec. 6 frees all edges).
+   free half period onto the other half, Supplement Sec. 7 frees all edges).
    edges: n_edges float64 (host or device), positions in pixels measured from
    the mirror plane x = nx/2, nondecreasing, ridge i = [t_2i, t_2i+1];
    -nx/2 <= t_0 and t_last <= 0 (mirror != 0) or <= nx/2 (mirror == 0).
@@ -236,6 +250,20 @@ int apf_set_krylov(apf_ctx *ctx, int m);
    time into factorization and post-processing, Supplement Table S1), kernel
    launches and the workspace size.  *stats is written; APF_EINVAL for NULL. */
 int apf_get_stats(const apf_ctx *ctx, apf_stats *stats);
+
+/* Mixed mode: storage of the slab Schur blocks.  Every field sweep needs the
+   inverses G_j of all h slab rows (the blocks the partial factorization of
+   paper Sec. 2 leaves behind; 16 nx^2 bytes each in packed bf16 form, 21.5 GB
+   for h = 20 at nx = 8192).  segment_rows = 0 (the default) stores all h.
+   segment_rows = k in [1, h) keeps the packed inverses of only one segment of
+   k rows, plus the float32 G_{c-1} (8 nx^2 bytes) at every segment start
+   c > 0, and recomputes a segment's inverses from its checkpoint whenever a
+   sweep needs them: about two eliminations more per sweep, for a workspace
+   of (k * 16 + (ceil(h/k) - 1) * 8) nx^2 bytes instead of h * 16 nx^2.  The
+   recomputed inverses are bit-identical to the stored ones, so results do
+   not change.  Re-creates the workspace like apf_set_krylov (the fields of
+   an earlier solve are gone).  APF_EINVAL in APF_FP64 mode for k != 0. */
+int apf_set_schur_storage(apf_ctx *ctx, int segment_rows);
 
 /* Measurement support (no counterpart in the paper).  When enabled, every
    tensor-core GEMM launch of later solves is bracketed by CUDA events on the

@@ -3,7 +3,7 @@
 The paper's beam splitter (Sec. 3, Eq. 5) is parametrized by the edge
 positions p = {y_1, ..., y_N} of ridges in half a period, with the other half
 fixed by mirror symmetry {y_{N+1}, ..., y_{2N}} = -{y_N, ..., y_1}; without
-mirror symmetry (Supplement Sec. 6) all 2N edges are free.  The paper does not
+mirror symmetry (Supplement Sec. 7) all 2N edges are free.  The paper does not
 state how an edge that falls inside a pixel is discretized.  Reading used here:
 a pixel's permittivity is linear in the length of it that ridges cover,
 

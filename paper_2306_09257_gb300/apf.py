@@ -30,6 +30,7 @@ EXPORTS = ("apf_create", "apf_destroy", "apf_set_grid", "apf_set_eps", "apf_set_
            "apf_set_refinement", "apf_get_stats", "apf_set_profiling", "apf_get_profile",
            "apf_solve_S_noalloc", "apf_last_error", "apf_version", "apf_set_ridges", "apf_ridge_grad",
            "apf_substrate_orders", "apf_reflection", "apf_reverse_S", "apf_set_krylov",
+           "apf_solve_S_grad_adjoint", "apf_set_schur_storage",
            "apf_sno_create", "apf_sno_destroy", "apf_sno_num_params", "apf_sno_set_params",
            "apf_sno_get_params", "apf_sno_forward", "apf_sno_gradients", "apf_sno_train_step")
 
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.apf_get_channels.argtypes = [vp, ip, ip, ip, ip]
     L.apf_solve_S.argtypes = [vp, dp, vp]
     L.apf_solve_S_grad.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), i, dp, ctypes.POINTER(ctypes.c_double), dp, vp]
+    L.apf_solve_S_grad_adjoint.argtypes = L.apf_solve_S_grad.argtypes
     L.apf_grad_from_gamma.argtypes = [vp, dp, dp, vp]
     L.apf_set_refinement.argtypes = [vp, d, i]
     L.apf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
@@ -93,6 +95,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.apf_solve_S_noalloc.argtypes = [i, i, i, i, d, ctypes.POINTER(PML), dp, i, i, d, d, ip, i, ip, i, dp, vp]
     L.apf_substrate_orders.argtypes = [vp, ip, ip]
     L.apf_set_krylov.argtypes = [vp, i]
+    L.apf_set_schur_storage.argtypes = [vp, i]
     L.apf_reflection.argtypes = [vp, ip, i, dp, vp]
     L.apf_reverse_S.argtypes = [vp, dp, vp]
     L.apf_set_ridges.argtypes = [vp, dp, i, i, d, d, i, i, d, d, dp, vp]
@@ -254,6 +257,13 @@ class Solver:
     def set_refinement(self, tol: float, max_iters: int):
         self._check(self._L.apf_set_refinement(self._h, float(tol), int(max_iters)))
 
+    def set_schur_storage(self, segment_rows: int):
+        """Mixed mode: 0 stores every slab inverse; k > 0 keeps one segment of
+        k rows and recomputes the others from float32 checkpoints (see
+        apf_set_schur_storage)."""
+        self._check(self._L.apf_set_schur_storage(self._h, int(segment_rows)))
+        self.version += 1
+
     def set_krylov(self, m: int):
         """Mixed mode: GMRES(m) refinement (0: plain refinement); see apf_set_krylov."""
         self._check(self._L.apf_set_krylov(self._h, int(m)))
@@ -286,6 +296,22 @@ class Solver:
         self.version += 1
         self._check(self._L.apf_solve_S_grad(self._h, oid, params, npar, _ptr(S, np.complex128),
                                              ctypes.byref(f), _ptr(g, np.float64), st),
+                    allow=(APF_ENOCONV,) if allow_noconv else ())
+        return S, f.value, g
+
+    def solve_S_grad_adjoint(self, kind: str, orders: Sequence[int], target: float = 0.0,
+                             out_S=None, out_grad=None, allow_noconv=False):
+        """S, f and df/deps by the conventional adjoint method (Eq. S1: a
+        forward sweep, then an adjoint sweep with sources built from Gamma);
+        the paper's baseline for APF, on the same elimination."""
+        S = self._alloc_S() if out_S is None else out_S
+        g = np.empty((self.h, self.nx), dtype=np.float64) if out_grad is None else out_grad
+        oid, params, npar = self.objective_params(kind, orders, target)
+        f = ctypes.c_double()
+        st = _stream_of(S, g)
+        self.version += 1
+        self._check(self._L.apf_solve_S_grad_adjoint(self._h, oid, params, npar, _ptr(S, np.complex128),
+                                                     ctypes.byref(f), _ptr(g, np.float64), st),
                     allow=(APF_ENOCONV,) if allow_noconv else ())
         return S, f.value, g
 

@@ -101,7 +101,9 @@ static int ensure_workspace(apf_ctx *c) {
         AL(c->d_G, h * nx * nx);
         AL(c->d_scr1, nx * nx / 2); AL(c->d_scr2, nx * nx / 2);
     }
-    AL(c->d_E, h * ncol * nx); AL(c->d_T, ncol * nx); AL(c->d_fft, ncol * nx);
+    // fields: the single-elimination solve's n_in + n_out columns, or the
+    // conventional adjoint method's n_in forward and n_in adjoint columns
+    AL(c->d_E, h * std::max<long long>(ncol, 2LL * nin) * nx); AL(c->d_T, ncol * nx); AL(c->d_fft, ncol * nx);
     if (c->precision != APF_FP64) { AL(c->d_R, h * ncol * nx); }
     AL(c->d_S, (long long)nout * nin); AL(c->d_Gam, (long long)nout * nin);
     AL(c->d_Q, h * nout * nx); AL(c->d_grad, h * nx);
@@ -331,6 +333,20 @@ int apf_set_krylov(apf_ctx *c, int m) {
     return ensure_workspace(c);
 }
 
+int apf_set_schur_storage(apf_ctx *c, int segment_rows) {
+    if (!c) return APF_EINVAL;
+    if (segment_rows < 0 || segment_rows > 4096)
+        return set_err(c, APF_EINVAL, "segment_rows=%d must be in [0, 4096]", segment_rows);
+    if (c->precision == APF_FP64 && segment_rows != 0)
+        return set_err(c, APF_EINVAL, "recomputation of the slab inverses applies to the mixed mode only");
+    if (segment_rows == c->schur_seg) return APF_OK;
+    c->schur_seg = segment_rows;
+    if (c->ws_nx < 0) return APF_OK;  // allocated with the workspace at apf_set_channels
+    cudaSetDevice(c->device);
+    free_workspace(c);
+    return ensure_workspace(c);
+}
+
 int apf_set_profiling(apf_ctx *c, int enable) {
     if (!c) return APF_EINVAL;
     cudaSetDevice(c->device);
@@ -368,34 +384,35 @@ int apf_get_stats(const apf_ctx *c, apf_stats *st) {
 // Solve pipeline
 // ---------------------------------------------------------------------------
 void fields64(apf_ctx *c, cudaStream_t s) {
-    int nin = c->nin, nout = c->nout, ncol = nin + nout;
+    int nf = c->cf, ncol = c->cf + c->ca;
     long long nx = c->nx, L = (long long)ncol * nx, nn = nx * nx;
+    double2 *E = c->d_Ew;
     const double2 one = cmk(1, 0), zero = cmk(0, 0);
-    // forward chain Y_j = G_{j-1} Y_{j-1} (input columns; Y_0 = R_0)
+    // forward chain Y_j = G_{j-1} Y_{j-1} (forward columns; Y_0 = R_0)
     for (int j = 1; j < c->h; ++j)
-        zgemm(c, false, false, nin, c->nx, c->nx, one, c->d_E + (j - 1) * L, nx, 0, c->d_G + (j - 1) * nn, nx, 0,
-              zero, c->d_E + j * L, nx, 0, 1, s);
+        zgemm(c, false, false, nf, c->nx, c->nx, one, E + (j - 1) * L, nx, 0, c->d_G + (j - 1) * nn, nx, 0,
+              zero, E + j * L, nx, 0, 1, s);
     // back substitution E_{h-1} = G_{h-1} Y_{h-1}; E_j = G_j (Y_j + E_{j+1})
     for (int j = c->h - 1; j >= 0; --j) {
-        if (j == c->h - 1) launch_copy(c, c->d_T, c->d_E + j * L, L, s);
-        else launch_add(c, c->d_T, c->d_E + j * L, c->d_E + (j + 1) * L, L, s);
+        if (j == c->h - 1) launch_copy(c, c->d_T, E + j * L, L, s);
+        else launch_add(c, c->d_T, E + j * L, E + (j + 1) * L, L, s);
         zgemm(c, false, false, ncol, c->nx, c->nx, one, c->d_T, nx, 0, c->d_G + j * nn, nx, 0, zero,
-              c->d_E + j * L, nx, 0, 1, s);
+              E + j * L, nx, 0, 1, s);
     }
 }
 
 // Everything up to the first host synchronization: boundary elimination, slab
-// elimination and the first field sweep.  Captured once into a CUDA graph.
+// elimination and the first field sweep of the current column layout (0 or 1).
+// Captured once per layout into a CUDA graph.
 static int main_body(apf_ctx *c, cudaStream_t s) {
-    int nin = c->nin, nout = c->nout, ncol = nin + nout;
-    long long nx = c->nx, L = (long long)ncol * nx;
+    long long L = (long long)(c->cf + c->ca) * c->nx;
     cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), s);
     record_event(c, c->ev[0], s);
     launch_boundary(c, s);
     record_event(c, c->ev[1], s);
     int rc = APF_OK;
     if (c->precision == APF_FP64) {
-        long long nn = nx * nx;
+        long long nx = c->nx, nn = nx * nx;
         for (int j = 0; j < c->h; ++j) {
             double2 *X = c->d_G + j * nn;
             launch_assemble64(c, j, X, j > 0 ? c->d_G + (j - 1) * nn : nullptr, s);
@@ -406,14 +423,38 @@ static int main_body(apf_ctx *c, cudaStream_t s) {
         if (rc != APF_OK) return rc;
     }
     record_event(c, c->ev[2], s);
-    launch_zero(c, c->d_E, sizeof(double2) * c->h * L, s);
-    launch_build_rhs(c, c->d_E, s);
+    launch_zero(c, c->d_Ew, sizeof(double2) * c->h * L, s);
+    launch_build_rhs(c, c->d_Ew, s);
     if (c->precision == APF_FP64) fields64(c, s);
     else rc = mixed_fields_begin(c, s);
     return rc;
 }
 
-static int run_solve(apf_ctx *c, cudaStream_t s) {
+// Second pass of the conventional adjoint method (layout 2): the adjoint
+// sources C_a^adj = sum_b Gamma_ba C_b on the last slab row, then the field
+// sweep through the stored elimination.
+static int adjoint_body(apf_ctx *c, cudaStream_t s) {
+    long long L = (long long)(c->cf + c->ca) * c->nx;
+    launch_zero(c, c->d_Ew, sizeof(double2) * c->h * L, s);
+    launch_adjoint_rhs(c, c->d_Gam, c->d_Ew + (long long)(c->h - 1) * L, s);
+    if (c->precision == APF_FP64) {
+        fields64(c, s);
+        return APF_OK;
+    }
+    return mixed_fields_begin(c, s);
+}
+
+static void set_layout(apf_ctx *c, int lay) {
+    c->lay = lay;
+    if (lay == 0) { c->cf = c->nin; c->ca = c->nout; c->d_Ew = c->d_E; }
+    else if (lay == 1) { c->cf = c->nin; c->ca = 0; c->d_Ew = c->d_E; }
+    else { c->cf = 0; c->ca = c->nin; c->d_Ew = c->d_E + (long long)c->h * c->nin * c->nx; }
+}
+
+// One pass of the solve in column layout `lay` (0: the single elimination,
+// 1: the forward pass of the conventional adjoint method): elimination and
+// field sweep, refinement (mixed), S readout.
+static int run_solve(apf_ctx *c, cudaStream_t s, int lay = 0) {
     if (!c->grid_set || !c->eps_set || !c->ch_set)
         return set_err(c, APF_ESTATE, "solve needs apf_set_grid, apf_set_eps and apf_set_channels");
     cudaSetDevice(c->device);
@@ -421,7 +462,9 @@ static int run_solve(apf_ctx *c, cudaStream_t s) {
     c->prof_used = c->prof_static;
     c->stats.refine_iters = 0;
     c->stats.residual = 0.0;
-    int rc = run_graph(c, c->g_main, s, main_body);
+    c->fields_lay = -1;
+    set_layout(c, lay);
+    int rc = run_graph(c, c->g_main[lay], s, main_body);
     if (rc != APF_OK) return rc;
     if (c->precision != APF_FP64) {
         rc = mixed_refine(c, s);
@@ -430,6 +473,7 @@ static int run_solve(apf_ctx *c, cudaStream_t s) {
     cudaEventRecord(c->ev[3], s);
     launch_readout(c, s);
     cudaEventRecord(c->ev[4], s);
+    c->fields_lay = lay;
     return rc;
 }
 
@@ -439,9 +483,11 @@ void record_event(apf_ctx *c, cudaEvent_t e, cudaStream_t s) {
 }
 
 void graphs_reset(apf_ctx *c) {
-    for (GraphSlot *g : {&c->g_main, &c->g_resid, &c->g_correct}) {
-        if (g->exec) cudaGraphExecDestroy(g->exec);
-        *g = GraphSlot{};
+    for (int l = 0; l < 3; ++l) {
+        for (GraphSlot *g : {&c->g_main[l], &c->g_resid[l], &c->g_correct[l]}) {
+            if (g->exec) cudaGraphExecDestroy(g->exec);
+            *g = GraphSlot{};
+        }
     }
     c->prof_static = 0;
     c->prof_used = 0;
@@ -585,10 +631,68 @@ int apf_solve_S_grad(apf_ctx *c, int objective, const double *params, int n_para
     return r;
 }
 
+// The conventional adjoint method (paper Supplement Sec. 1, Eq. S1) on the same
+// elimination: forward fields of the n_in inputs (with their own refinement),
+// S, f and Gamma, then a second sweep of n_in adjoint fields whose sources
+// C_a^adj = sum_b Gamma_ba C_b are known only after Gamma, and the elementwise
+// contraction of forward and adjoint fields.
+static int adjoint_method(apf_ctx *c, int objective, const double *params, int n_params, cudaStream_t s,
+                          int *rc_solve) {
+    int rc = run_solve(c, s, 1);
+    if (rc != APF_OK && rc != APF_ENOCONV) return rc;
+    *rc_solve = rc;
+    const int it1 = c->stats.refine_iters;
+    const double res1 = c->stats.residual;
+    rc = launch_objective(c, objective, params, n_params, s);
+    if (rc != APF_OK) return rc;
+    c->fields_lay = -1;
+    set_layout(c, 2);
+    rc = run_graph(c, c->g_main[2], s, adjoint_body);
+    if (rc != APF_OK) return rc;
+    if (c->precision != APF_FP64) {
+        rc = mixed_refine(c, s);
+        if (rc != APF_OK && rc != APF_ENOCONV) return rc;
+        if (rc == APF_ENOCONV) *rc_solve = rc;
+    }
+    c->stats.refine_iters += it1;
+    c->stats.residual = std::max(c->stats.residual, res1);
+    launch_gradient_adjoint(c, c->d_E, c->d_Ew, s);
+    set_layout(c, 1);
+    c->fields_lay = 1;
+    return APF_OK;
+}
+
+int apf_solve_S_grad_adjoint(apf_ctx *c, int objective, const double *params, int n_params, double *S, double *f,
+                             double *grad_eps, void *stream) {
+    if (!c) return APF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!grad_eps) return set_err(c, APF_EINVAL, "grad_eps is NULL");
+    if (!c->grid_set || !c->eps_set || !c->ch_set)
+        return set_err(c, APF_ESTATE, "solve needs apf_set_grid, apf_set_eps and apf_set_channels");
+    if (objective != APF_OBJ_POWER && objective != APF_OBJ_SPLITTER)
+        return set_err(c, APF_EINVAL, "unknown objective id %d", objective);
+    if (!params || n_params < 2 || (int)params[1] < 1 || (int)params[1] > 16 || n_params != 2 + (int)params[1])
+        return set_err(c, APF_EINVAL, "objective params must be {t, nD, d_1..d_nD} with 1 <= nD <= 16");
+    int rc_solve = APF_OK;
+    int rc = adjoint_method(c, objective, params, n_params, s, &rc_solve);
+    if (rc != APF_OK) { cudaStreamSynchronize(s); return rc; }
+    cudaEventRecord(c->ev[5], s);
+    size_t sb = sizeof(double2) * (size_t)c->nin * c->nout;
+    if (S) cudaMemcpyAsync(S, c->d_S, sb, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(grad_eps, c->d_grad, sizeof(double) * c->h * c->nx, cudaMemcpyDefault, s);
+    double fh = 0.0;
+    cudaMemcpyAsync(&fh, c->d_f, sizeof(double), cudaMemcpyDeviceToHost, s);
+    int r = finish(c, s, rc_solve);
+    if (f) *f = fh;
+    return r;
+}
+
 int apf_grad_from_gamma(apf_ctx *c, const double *Gamma, double *grad_eps, void *stream) {
     if (!c) return APF_EINVAL;
     if (!Gamma || !grad_eps) return set_err(c, APF_EINVAL, "Gamma / grad_eps is NULL");
     if (!c->ch_set || c->ws_nx < 0) return set_err(c, APF_ESTATE, "apf_grad_from_gamma needs a previous solve");
+    if (c->fields_lay != 0)
+        return set_err(c, APF_ESTATE, "apf_grad_from_gamma needs the fields of apf_solve_S or apf_solve_S_grad");
     cudaStream_t s = (cudaStream_t)stream;
     cudaSetDevice(c->device);
     size_t sb = sizeof(double2) * (size_t)c->nin * c->nout;
@@ -627,7 +731,8 @@ int apf_substrate_orders(const apf_ctx *c, int *n, int *m) {
 int apf_reflection(apf_ctx *c, const int *m_ref, int n_ref, double *R, void *stream) {
     if (!c) return APF_EINVAL;
     if (!R) return set_err(c, APF_EINVAL, "R is NULL");
-    if (!c->ch_set || c->ws_nx < 0) return set_err(c, APF_ESTATE, "apf_reflection needs a previous solve");
+    if (!c->ch_set || c->ws_nx < 0 || c->fields_lay < 0)
+        return set_err(c, APF_ESTATE, "apf_reflection needs a previous solve");
     std::vector<int> ord;
     if (m_ref && n_ref > 0) {
         if (n_ref > c->nx) return set_err(c, APF_EINVAL, "n_ref=%d exceeds nx=%d", n_ref, c->nx);
@@ -662,7 +767,8 @@ int apf_reflection(apf_ctx *c, const int *m_ref, int n_ref, double *R, void *str
 int apf_reverse_S(apf_ctx *c, double *S_rev, void *stream) {
     if (!c) return APF_EINVAL;
     if (!S_rev) return set_err(c, APF_EINVAL, "S_rev is NULL");
-    if (!c->ch_set || c->ws_nx < 0) return set_err(c, APF_ESTATE, "apf_reverse_S needs a previous solve");
+    if (!c->ch_set || c->ws_nx < 0 || c->fields_lay != 0)
+        return set_err(c, APF_ESTATE, "apf_reverse_S needs the fields of apf_solve_S or apf_solve_S_grad");
     std::vector<int> rmap(c->nout);
     for (int q = 0; q < c->nout; ++q) {
         int hit = -1;

@@ -81,6 +81,7 @@ struct apf_ctx {
     double ir_tol = 1e-10;
     int ir_max = 40;
     int krylov_m = 0;  // mixed mode: GMRES(m) refinement when > 0
+    int schur_seg = 0; // mixed mode: recompute the slab inverses in segments of this many rows (0: store all)
     // workspace signature
     int ws_nx = -1, ws_ny = -1, ws_h = -1, ws_min = -1, ws_mout = -1;
     long long ws_bytes = 0;
@@ -118,11 +119,20 @@ struct apf_ctx {
     int ridge_n = 0, ridge_cap = 0, ridge_h = 0, ridge_mirror = 0;
     long long ridge_eps_cap = 0;
     double ridge_eps_r = 0, ridge_eps_b = 0;
-    // CUDA graphs (captured on cap_stream, replayed on the caller's stream)
+    // Column layout of the slab fields being swept: cf forward columns (sources
+    // on the first slab row) followed by ca adjoint columns (sources on the last
+    // slab row), stored at d_Ew as [row][cf + ca][x].  The single-elimination
+    // solve sweeps (n_in, n_out) at d_E (layout 0).  The conventional adjoint
+    // method sweeps (n_in, 0) at d_E (layout 1), then (0, n_in) at
+    // d_E + h n_in nx (layout 2).
+    int lay = 0, cf = 0, ca = 0;
+    double2 *d_Ew = nullptr;
+    int fields_lay = -1;  // layout of the fields the last solve left (0 or 1; -1: none)
+    // CUDA graphs (captured on cap_stream, replayed on the caller's stream), one per layout
     cudaStream_t cap_stream = nullptr;
     bool use_graphs = true;
     bool capturing = false;
-    GraphSlot g_main, g_resid, g_correct;
+    GraphSlot g_main[3], g_resid[3], g_correct[3];
     // GEMM launch profiling
     int prof_static = 0;  // pairs reserved by captured graphs
     bool prof_on = false;
@@ -151,6 +161,7 @@ GridDev make_grid(const apf_ctx *c);
 // boundary.cu
 void launch_boundary(apf_ctx *c, cudaStream_t s);
 void launch_build_rhs(apf_ctx *c, double2 *E, cudaStream_t s);
+void launch_adjoint_rhs(apf_ctx *c, const double2 *Gamma, double2 *E, cudaStream_t s);
 void launch_source_row(apf_ctx *c, double2 *q, cudaStream_t s);
 void launch_reflection(apf_ctx *c, const double2 *fft0, const double2 *q, const int *m_ref, int n_ref, double2 *R,
                        cudaStream_t s);
@@ -177,6 +188,7 @@ void fields64(apf_ctx *c, cudaStream_t s);
 void launch_readout(apf_ctx *c, cudaStream_t s);  // S from fields
 int launch_objective(apf_ctx *c, int objective, const double *params, int n_params, cudaStream_t s);
 int launch_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s);
+void launch_gradient_adjoint(apf_ctx *c, const double2 *Fw, const double2 *Lam, cudaStream_t s);
 int mixed_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s);
 
 // mixed.cu

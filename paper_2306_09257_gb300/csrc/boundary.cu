@@ -132,6 +132,17 @@ __global__ void k_build_rhs(GridDev g, const int *m_in, int n_in, const int *m_o
     E[((long long)row * ncol + c) * g.nx + x] = v;
 }
 
+// spec[a][(-m_b) mod nx] = Gamma[b][a] * w_b (output orders are distinct, so
+// every (a, b) writes its own element).
+__global__ void k_adjoint_spectrum(const double2 *Gamma, const double2 *coef, const int *m_out, int n_in, int n_out,
+                                   int nx, double2 *spec) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    int b = blockIdx.y;
+    if (a >= n_in) return;
+    int m = mod_nx(-m_out[b], nx);
+    spec[(long long)a * nx + m] = cmul(Gamma[(long long)b * n_in + a], coef[n_in + b]);
+}
+
 __global__ void k_twiddles(double2 *tw, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n / 2) return;
@@ -283,9 +294,23 @@ void launch_boundary(apf_ctx *c, cudaStream_t s) {
 
 void launch_build_rhs(apf_ctx *c, double2 *E, cudaStream_t s) {
     GridDev g = make_grid(c);
+    // the columns of the current layout: cf forward (inputs), ca adjoint (outputs)
+    int nf = c->cf, na = c->ca;
+    dim3 grid((c->nx + 255) / 256, nf + na);
+    APF_LAUNCH(c, k_build_rhs, grid, 256, 0, s, g, c->d_min, nf, c->d_mout, na, c->d_coef, E);
+}
+
+// Right-hand sides of the conventional adjoint method's second pass (Eq. S1):
+// for input a, the adjoint source sum_b Gamma_ba C_b^T carried to the last slab
+// row, i.e. sum_b Gamma_ba w_b u_{-m_b} (the adjoint column of output b is
+// w_b u_{-m_b} on that row).  Written as a spectrum (order -m_b gets
+// Gamma_ba w_b) and brought to pixels by one inverse FFT per column.
+void launch_adjoint_rhs(apf_ctx *c, const double2 *Gamma, double2 *Erow, cudaStream_t s) {
     int nin = c->nin, nout = c->nout;
-    dim3 grid((c->nx + 255) / 256, nin + nout);
-    APF_LAUNCH(c, k_build_rhs, grid, 256, 0, s, g, c->d_min, nin, c->d_mout, nout, c->d_coef, E);
+    launch_zero(c, c->d_fft, sizeof(double2) * (long long)nin * c->nx, s);
+    dim3 grid((nin + 127) / 128, nout);
+    APF_LAUNCH(c, k_adjoint_spectrum, grid, 128, 0, s, Gamma, c->d_coef, c->d_mout, nin, nout, c->nx, c->d_fft);
+    launch_fft(c, c->d_fft, Erow, c->nx, nin, c->nx, c->nx, +1, 1.0 / sqrt((double)c->nx), s);
 }
 
 void boundary_init_attrs() {

@@ -26,8 +26,15 @@ struct MixedWork {
     float *Vre = nullptr, *Vim = nullptr;
     __nv_bfloat16 *PA = nullptr, *PB = nullptr;      // operand packs
     long long pa_elems = 0, pb_elems = 0;
-    __nv_bfloat16 *GP = nullptr;                     // packed G_j, h of them
+    __nv_bfloat16 *GP = nullptr;                     // packed G_j: h of them, or seg_rows when recomputing
     long long gp_stride = 0;
+    // Recomputation of the slab Schur blocks (seg_rows > 0): the rows are cut
+    // into segments of seg_rows; only the packed inverses of one segment are
+    // held (GP slot j - start of j's segment), plus the float32 G_{c-1} at every
+    // segment start c > 0 (checkpoint s-1 for segment s), from which a
+    // segment's inverses are recomputed when a sweep needs them.
+    int seg_rows = 0, nseg = 1, seg_loaded = -1;
+    float *CK = nullptr;                             // (nseg - 1) checkpoints, 2 n^2 floats each
     float *O32 = nullptr;                            // GEMM output planes, 2 * max(ncol, n_out) * nx
     double2 *r = nullptr, *delta = nullptr;          // refinement buffers (h*ncol*nx)
     double2 *cb = nullptr, *ct = nullptr;            // circulant products on the boundary rows
@@ -38,6 +45,8 @@ struct MixedWork {
     double *knrm = nullptr;                          // ||W_c||^2 per Arnoldi step, km*ncol
     std::vector<void *> allocs;
 };
+
+int recompute_segment(apf_ctx *c, int seg, cudaStream_t s);
 
 namespace {
 
@@ -721,29 +730,48 @@ int inv32(apf_ctx *c, const PV &X, int n, float *Tre, float *Tim, float *Vre, fl
 
 // E ~= Khat^-1 Rin with the stored G_j (block forward sweep + back
 // substitution).  mcols: columns that the forward sweep must carry.
+// Packed operand view of G_j (slot j, or j's slot in its segment).
+PackView gp_view(const apf_ctx *c, int j) {
+    const MixedWork *w = c->mw;
+    const long long rows = 2LL * c->nx, kp = 2LL * c->nx;
+    const int slot = w->seg_rows > 0 ? j % w->seg_rows : j;
+    return PackView{w->GP + slot * w->gp_stride, rows, kp, w->nsplit_elim, rows * kp};
+}
+
+// E ~= Khat^-1 Rin with the stored (or recomputed) G_j (block forward sweep +
+// back substitution).  mcols: columns that the forward sweep must carry.
 int approx_solve(apf_ctx *c, const double2 *Rin, double2 *Eout, int mcols, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int nin = c->nin, nout = c->nout, ncol = nin + nout;
+    int ncol = c->cf + c->ca;
     int nx = c->nx, ns = w->nsplit_elim;
     long long L = (long long)ncol * nx;
     float *Ore = w->O32, *Oim = w->O32 + L;
-    long long gp_rows = 2LL * nx, gp_kp = 2LL * nx;
-    auto gview = [&](int j) {
-        return PackView{w->GP + j * w->gp_stride, gp_rows, gp_kp, ns, gp_rows * gp_kp};
+    const int K = w->seg_rows;
+    // with recomputation: the segment whose inverses row j needs must be loaded
+    auto need = [&](int j) -> int {
+        if (K <= 0) return APF_OK;
+        const int sg = j / K;
+        if (sg == w->seg_loaded) return APF_OK;
+        return recompute_segment(c, sg, s);
     };
     dim3 cgrid((nx + 255) / 256, ncol);
     cudaMemcpyAsync(Eout, Rin, sizeof(double2) * L, cudaMemcpyDeviceToDevice, s);
     int rc;
     for (int j = 1; j < c->h; ++j) {
-        PackView pa = pack64A(c, w->PA, Eout + (j - 1) * L, nullptr, nx, mcols, nx, ns, s);
-        if ((rc = tc_gemm(c, pa, gview(j - 1), ns, mcols, 2 * nx, nx, 1.f, 0.f, Ore, Oim, nx, nullptr, nullptr, 0, s)))
-            return rc;
+        if (mcols > 0) {
+            if ((rc = need(j - 1))) return rc;
+            PackView pa = pack64A(c, w->PA, Eout + (j - 1) * L, nullptr, nx, mcols, nx, ns, s);
+            if ((rc = tc_gemm(c, pa, gp_view(c, j - 1), ns, mcols, 2 * nx, nx, 1.f, 0.f, Ore, Oim, nx, nullptr,
+                              nullptr, 0, s)))
+                return rc;
+        }
         APF_LAUNCH(c, k_combine, cgrid, 256, 0, s, Eout + j * L, Rin + j * L, Ore, Oim, ncol, mcols, nx);
     }
     for (int j = c->h - 1; j >= 0; --j) {
+        if ((rc = need(j))) return rc;
         const double2 *s2 = (j == c->h - 1) ? nullptr : Eout + (j + 1) * L;
         PackView pa = pack64A(c, w->PA, Eout + j * L, s2, nx, ncol, nx, ns, s);
-        if ((rc = tc_gemm(c, pa, gview(j), ns, ncol, 2 * nx, nx, 1.f, 0.f, Ore, Oim, nx, nullptr, nullptr, 0, s)))
+        if ((rc = tc_gemm(c, pa, gp_view(c, j), ns, ncol, 2 * nx, nx, 1.f, 0.f, Ore, Oim, nx, nullptr, nullptr, 0, s)))
             return rc;
         APF_LAUNCH(c, k_combine, cgrid, 256, 0, s, Eout + j * L, (const double2 *)nullptr, Ore, Oim, ncol, ncol, nx);
     }
@@ -752,7 +780,7 @@ int approx_solve(apf_ctx *c, const double2 *Rin, double2 *Eout, int mcols, cudaS
 
 int residual(apf_ctx *c, const double2 *E, double2 *r, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int nin = c->nin, nout = c->nout, ncol = nin + nout;
+    int ncol = c->cf + c->ca;
     int nx = c->nx;
     long long L = (long long)ncol * nx;
     int logn = 0;
@@ -814,7 +842,10 @@ int mixed_alloc(apf_ctx *c) {
     WA(w->PA, w->pa_elems);
     WA(w->PB, w->pb_elems);
     w->gp_stride = 2 * n * 2 * n * w->nsplit_elim;
-    WA(w->GP, h * w->gp_stride);
+    w->seg_rows = (c->schur_seg > 0 && c->schur_seg < h) ? c->schur_seg : 0;
+    w->nseg = w->seg_rows > 0 ? (int)((h + w->seg_rows - 1) / w->seg_rows) : 1;
+    WA(w->GP, (w->seg_rows > 0 ? w->seg_rows : h) * w->gp_stride);
+    if (w->seg_rows > 0) { WA(w->CK, (long long)(w->nseg - 1) * 2 * n * n); }
     WA(w->O32, 2 * std::max<long long>(ncol, nout) * n);
     WA(w->r, h * ncol * n); WA(w->delta, h * ncol * n);
     WA(w->cb, ncol * n); WA(w->ct, ncol * n);
@@ -836,6 +867,8 @@ int mixed_eliminate(apf_ctx *c, cudaStream_t s) {
     if (!w) return set_err(c, APF_ESTATE, "mixed workspace missing");
     GridDev g = make_grid(c);
     int n = c->nx;
+    const long long nn = (long long)n * n;
+    const int K = w->seg_rows;
     dim3 agrid((n / 4 + 255) / 256, n);
     PV X{w->Xre, w->Xim, n};
     APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, 0, c->d_eps, c->d_circ, (const float *)nullptr,
@@ -843,11 +876,44 @@ int mixed_eliminate(apf_ctx *c, cudaStream_t s) {
     for (int j = 0; j < c->h; ++j) {
         int rc = inv32(c, X, n, w->Tre, w->Tim, w->Vre, w->Vim, s);
         if (rc) return rc;
-        pack32(c, w->GP + j * w->gp_stride, X, n, n, false, true, w->nsplit_elim, s);
+        pack32(c, (__nv_bfloat16 *)gp_view(c, j).base, X, n, n, false, true, w->nsplit_elim, s);
+        if (K > 0 && j + 1 < c->h && (j + 1) % K == 0) {
+            // checkpoint G_j (float32) for the segment that starts at row j + 1
+            float *ck = w->CK + (long long)((j + 1) / K - 1) * 2 * nn;
+            cudaMemcpyAsync(ck, w->Xre, sizeof(float) * nn, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(ck + nn, w->Xim, sizeof(float) * nn, cudaMemcpyDeviceToDevice, s);
+        }
         if (j + 1 < c->h)
             APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, j + 1, c->d_eps, c->d_circ, w->Xre, w->Xim, w->Xre,
                        w->Xim);
     }
+    w->seg_loaded = K > 0 ? (c->h - 1) / K : -1;
+    return APF_OK;
+}
+
+// Recompute the packed inverses of segment `seg` (rows c .. c + seg_rows - 1)
+// into the GP slots: X_c = K_c - G_{c-1} from the float32 checkpoint, then the
+// same inversions and assemblies as the elimination (bit-identical results).
+int recompute_segment(apf_ctx *c, int seg, cudaStream_t s) {
+    MixedWork *w = c->mw;
+    GridDev g = make_grid(c);
+    const int n = c->nx, K = w->seg_rows;
+    const long long nn = (long long)n * n;
+    const int r0 = seg * K, r1 = std::min(c->h, r0 + K);
+    dim3 agrid((n / 4 + 255) / 256, n);
+    PV X{w->Xre, w->Xim, n};
+    const float *gre = seg > 0 ? w->CK + (long long)(seg - 1) * 2 * nn : nullptr;
+    const float *gim = seg > 0 ? gre + nn : nullptr;
+    APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, r0, c->d_eps, c->d_circ, gre, gim, w->Xre, w->Xim);
+    for (int j = r0; j < r1; ++j) {
+        int rc = inv32(c, X, n, w->Tre, w->Tim, w->Vre, w->Vim, s);
+        if (rc) return rc;
+        pack32(c, (__nv_bfloat16 *)gp_view(c, j).base, X, n, n, false, true, w->nsplit_elim, s);
+        if (j + 1 < r1)
+            APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, j + 1, c->d_eps, c->d_circ, w->Xre, w->Xim, w->Xre,
+                       w->Xim);
+    }
+    w->seg_loaded = seg;
     return APF_OK;
 }
 
@@ -855,28 +921,28 @@ int mixed_eliminate(apf_ctx *c, cudaStream_t s) {
 // the first low-precision solve E = Khat^-1 R.
 int mixed_fields_begin(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int nin = c->nin, nout = c->nout, ncol = nin + nout;
+    int ncol = c->cf + c->ca;
     long long total = (long long)ncol * c->nx * c->h;
-    cudaMemcpyAsync(c->d_R, c->d_E, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(c->d_R, c->d_Ew, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s);
     APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, c->d_R, c->h, ncol, c->nx, w->rnorm);
-    return approx_solve(c, c->d_R, c->d_E, nin, s);
+    return approx_solve(c, c->d_R, c->d_Ew, c->cf, s);
 }
 
 static int resid_body(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int ncol = (c->nin + c->nout);
-    residual(c, c->d_E, w->r, s);
+    int ncol = c->cf + c->ca;
+    residual(c, c->d_Ew, w->r, s);
     APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, c->nx, w->rnorm + ncol);
     return APF_OK;
 }
 
 static int correct_body(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
-    int ncol = (c->nin + c->nout);
+    int ncol = c->cf + c->ca;
     long long total = (long long)ncol * c->nx * c->h;
     int rc = approx_solve(c, w->r, w->delta, ncol, s);
     if (rc) return rc;
-    APF_LAUNCH(c, k_axpy, (unsigned)((total + 255) / 256), 256, 0, s, c->d_E, w->delta, total);
+    APF_LAUNCH(c, k_axpy, (unsigned)((total + 255) / 256), 256, 0, s, c->d_Ew, w->delta, total);
     return APF_OK;
 }
 
@@ -889,7 +955,7 @@ static const bool g_ir_verbose = [] {
 // K E (the slab operator in float64) into out.
 static int apply_K(apf_ctx *c, const double2 *E, double2 *out, cudaStream_t s) {
     MixedWork *w = c->mw;
-    const int ncol = c->nin + c->nout, nx = c->nx;
+    const int ncol = c->cf + c->ca, nx = c->nx;
     const long long L = (long long)ncol * nx;
     int logn = 0;
     while ((1 << logn) < nx) ++logn;
@@ -951,7 +1017,7 @@ static void hessenberg_lsq(int m, std::vector<std::complex<double>> &h, double b
 // are those of the plain refinement.
 static int mixed_refine_gmres(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
-    const int m = w->km, ncol = c->nin + c->nout, nx = c->nx;
+    const int m = w->km, ncol = c->cf + c->ca, nx = c->nx;
     const long long L = (long long)c->h * ncol * nx;
     const dim3 fgrid((nx + 255) / 256, ncol, c->h);
     std::vector<double> nr(ncol), ne(ncol), hn((size_t)m * ncol);
@@ -961,12 +1027,12 @@ static int mixed_refine_gmres(apf_ctx *c, cudaStream_t s) {
     double ratio = 0.0, prev = INFINITY;
     cudaMemcpyAsync(nr.data(), w->rnorm, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
     for (;;) {
-        residual(c, c->d_E, w->r, s);
+        residual(c, c->d_Ew, w->r, s);
         APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, nx, w->rnorm + ncol);
         cudaMemcpyAsync(ne.data(), w->rnorm + ncol, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return check_cuda(c, e, "refinement");
-        if (c->prof_on && iters == 0) prof_collect_range(c, c->g_main.prof_lo, c->g_main.prof_hi);
+        if (c->prof_on && iters == 0) prof_collect_range(c, c->g_main[c->lay].prof_lo, c->g_main[c->lay].prof_hi);
         ratio = 0.0;
         for (int i = 0; i < ncol; ++i) ratio = std::max(ratio, sqrt(ne[i] / std::max(nr[i], 1e-300)));
         if (g_ir_verbose)
@@ -1009,7 +1075,7 @@ static int mixed_refine_gmres(apf_ctx *c, cudaStream_t s) {
         }
         cudaMemcpyAsync(w->ky, yh.data(), sizeof(double2) * yh.size(), cudaMemcpyHostToDevice, s);
         for (int j = 0; j < m; ++j)
-            APF_LAUNCH(c, k_colaxpy, fgrid, 256, 0, s, c->d_E, w->KZ + j * L, w->ky + (long long)j * ncol, 1.0,
+            APF_LAUNCH(c, k_colaxpy, fgrid, 256, 0, s, c->d_Ew, w->KZ + j * L, w->ky + (long long)j * ncol, 1.0,
                        ncol, nx);
         iters += m;
     }
@@ -1023,18 +1089,18 @@ static int mixed_refine_gmres(apf_ctx *c, cudaStream_t s) {
 int mixed_refine(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
     if (w->km > 0) return mixed_refine_gmres(c, s);
-    int ncol = (c->nin + c->nout);
+    int ncol = c->cf + c->ca;
     std::vector<double> nr(ncol), ne(ncol);
     int iters = 0, rc, rising = 0;
     double ratio = 0.0, prev = INFINITY;
     for (;;) {
-        if ((rc = run_graph(c, c->g_resid, s, resid_body))) return rc;
+        if ((rc = run_graph(c, c->g_resid[c->lay], s, resid_body))) return rc;
         cudaMemcpyAsync(nr.data(), w->rnorm, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(ne.data(), w->rnorm + ncol, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return check_cuda(c, e, "refinement");
         if (c->prof_on) {
-            const GraphSlot &g = iters == 0 ? c->g_main : c->g_correct;
+            const GraphSlot &g = iters == 0 ? c->g_main[c->lay] : c->g_correct[c->lay];
             prof_collect_range(c, g.prof_lo, g.prof_hi);
         }
         ratio = 0.0;
@@ -1046,7 +1112,7 @@ int mixed_refine(apf_ctx *c, cudaStream_t s) {
         rising = ratio > prev ? rising + 1 : 0;
         if (rising >= 2) break;
         prev = ratio;
-        if ((rc = run_graph(c, c->g_correct, s, correct_body))) return rc;
+        if ((rc = run_graph(c, c->g_correct[c->lay], s, correct_body))) return rc;
         ++iters;
     }
     c->stats.refine_iters = iters;

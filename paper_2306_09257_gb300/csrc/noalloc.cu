@@ -142,6 +142,8 @@ extern "C" int apf_solve_S_noalloc(int nx, int ny, int npml_bot, int npml_top, d
     c.d_S = (double2 *)carve(sizeof(double2) * n_in * n_out);
     c.d_flags = (int *)carve(sizeof(int) * 4);
     if (off > kScratchBytes) return fail(APF_EINVAL, "problem does not fit the scratch array");
+    // one sweep of all forward and adjoint columns, as in apf_solve_S
+    c.lay = 0; c.cf = n_in; c.ca = n_out; c.d_Ew = c.d_E;
     // ---- the pipeline (same kernels as apf_solve_S in APF_FP64) ----
     cudaError_t ce = cudaMemcpyAsync(c.d_eps, eps_slab, sizeof(double) * h * n, cudaMemcpyDefault, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(c.d_min, ords_in, sizeof(int) * n_in, cudaMemcpyHostToDevice, s);

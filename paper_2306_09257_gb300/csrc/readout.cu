@@ -82,11 +82,35 @@ __global__ void k_grad_rowdot(const double2 *E, const double2 *Q, int h, int nx,
     g[(long long)j * nx + x] = 2.0 * k2 * acc;
 }
 
+// Conventional adjoint method (Eq. S1): g[j][x] = 2 k^2 Re sum_a lam_a[j][x] F_a[j][x],
+// with the forward fields F_a = A^-1 B_a and the adjoint fields
+// lam_a = A^-1 (C_a^adj)^T, C_a^adj = sum_b Gamma_ba C_b, both [row][a][x]
+// with n_in columns.  One thread per pixel, the sum over a in a fixed order.
+__global__ void k_grad_adjoint(const double2 *F, const double2 *Lam, int h, int nx, int n_in, double k2, double *g) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (x >= nx) return;
+    const long long o = (long long)j * n_in * nx + x;
+    double acc = 0.0;
+    for (int a = 0; a < n_in; ++a) {
+        const double2 f = F[o + (long long)a * nx], l = Lam[o + (long long)a * nx];
+        acc = fma(f.x, l.x, acc);
+        acc = fma(-f.y, l.y, acc);
+    }
+    g[(long long)j * nx + x] = 2.0 * k2 * acc;
+}
+
 }  // namespace
 
+void launch_gradient_adjoint(apf_ctx *c, const double2 *Fw, const double2 *Lam, cudaStream_t s) {
+    dim3 grid((c->nx + 255) / 256, c->h);
+    APF_LAUNCH(c, k_grad_adjoint, grid, 256, 0, s, Fw, Lam, c->h, c->nx, c->nin, c->k * c->k, c->d_grad);
+}
+
 void launch_readout(apf_ctx *c, cudaStream_t s) {
-    int nin = c->nin, nout = c->nout, ncol = nin + nout;
-    const double2 *Eh = c->d_E + (long long)(c->h - 1) * ncol * c->nx;
+    // forward columns come first in every layout that carries them (cf = n_in)
+    int nin = c->nin, nout = c->nout, ncol = c->cf + c->ca;
+    const double2 *Eh = c->d_Ew + (long long)(c->h - 1) * ncol * c->nx;
     launch_fft(c, Eh, c->d_fft, c->nx, nin, c->nx, c->nx, -1, 1.0 / sqrt((double)c->nx), s);
     dim3 grid((nin + 127) / 128, nout);
     APF_LAUNCH(c, k_gather_S, grid, 128, 0, s, c->d_fft, c->d_coef, c->d_mout, nin, nout, c->nx, c->d_S);

@@ -1,5 +1,5 @@
 // Ridge edge-position parametrization (paper Sec. 3, Eq. 5; mirror symmetry
-// of the free half period, Supplement Sec. 6 without it): the slab
+// of the free half period, Supplement Sec. 7 without it): the slab
 // permittivity of a ridge pattern and the chain rule from the pixel gradient
 // to the edge positions.
 #include "apf_internal.h"

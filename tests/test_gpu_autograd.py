@@ -174,3 +174,54 @@ def test_armijo_line_search_decreases_f(env):
     assert all(b <= a for a, b in zip(hist.f, hist.f[1:]))
     assert hist.f[-1] < hist.f[0]
     assert eps.min() >= 1.0 and eps.max() <= 2.25
+
+
+def test_multistart_on_one_gpu(env):
+    """Multi-start beam-splitter optimisation (Sec. 3) through the replica
+    helpers on one rank: every start is a seeded design optimised by the
+    Armijo line search on the GPU; the gathered best is the minimum final f
+    and every history decreases."""
+    torch, apf, AG = env
+    from paper_2306_09257_gb300 import replicas
+    w = W.TINY
+    s = apf.solver_for_workload(w, w.eps_slab(0), precision="mixed")
+    res = replicas.multistart(
+        lambda st: replicas.optimize_start(s, w, st, "splitter", [-1, 1], 0.25, iters=4), 3)
+    assert [r[0] for r in res["runs"]] == [0, 1, 2]
+    assert res["best_f"] == min(r[2] for r in res["runs"])
+    assert all(h[-1] < h[0] for _, _, _, h in res["runs"])
+    assert res["best_design"].shape == (w.h, w.nx)
+
+
+@pytest.mark.slow
+def test_central_fd_on_16_pixels_xlarge(env):
+    """The differentiation workload itself (8192 x 280, 20 x 8192 slab, 513 x
+    513 channels): central differences of the beam-splitter f (step 1e-6 in
+    eps) on 16 seeded pixels against the single-elimination gradient.  The
+    solves are refined to 1e-13 (float64 accuracy of S), so f's rounding noise
+    over 2h stays far below the gradient; the bound allows for the O(h^2)
+    truncation and that noise."""
+    torch, apf, AG = env
+    w = W.XLARGE
+    eps = w.eps_slab(3)
+    s = apf.solver_for_workload(w, eps, precision="mixed")
+    s.set_refinement(1e-13, 40)
+    orders = [-2, -1, 0, 1, 2]
+    _, f0, g = s.solve_S_grad("splitter", orders, 0.18, allow_noconv=True)
+    rng = np.random.default_rng(16)
+    pix = [(int(rng.integers(w.h)), int(rng.integers(w.nx))) for _ in range(16)]
+    h = 1e-6
+    fd = []
+    for (j, x) in pix:
+        vals = []
+        for sgn in (1, -1):
+            e = eps.copy()
+            e[j, x] += sgn * h
+            s.set_eps(e, w.eps_sub, w.eps_clad, j0=w.j0)
+            vals.append(s.solve_S_grad("splitter", orders, 0.18, allow_noconv=True)[1])
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    fd = np.array(fd)
+    ga = np.array([g[j, x] for j, x in pix])
+    err = np.linalg.norm(fd - ga) / np.linalg.norm(ga)
+    print(f"xlarge FD check: rel err {err:.2e}, |g| {np.linalg.norm(ga):.3e}")
+    assert err < 1e-4, err

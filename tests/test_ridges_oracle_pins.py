@@ -1,5 +1,5 @@
 """Pins of the ridge edge-position parametrization oracle (paper Sec. 3,
-Eq. 5: p = ridge edge positions, mirror symmetry; Supplement Sec. 6 without
+Eq. 5: p = ridge edge positions, mirror symmetry; Supplement Sec. 7 without
 it), checked against closed forms, exact special cases and finite
 differences of the oracle's own objective (not against the oracle's
 derivative formula)."""
