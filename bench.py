@@ -45,7 +45,8 @@ WL = {"mid": W.MID, "large": W.LARGE, "xlarge": W.XLARGE, "tiny": W.TINY}
 # capture of the field-sweep product (dram__bytes_read.sum + dram__bytes_write.sum
 # divided by 8 m n k x 3 plane products of that launch); a launch's traffic is
 # this times its flops.  None until a capture of the current kernel exists.
-GEMM_CAPTURE = {"bytes_per_hw_flop": None, "profile": "none"}
+GEMM_CAPTURE = {"bytes_per_hw_flop": 336.3e6 / (8.0 * 686 * 4096 * 4096 * 3),
+                "profile": "profiles/k_tc_gemm_pair_field_sweep_686x4096x4096.md"}
 
 
 def args_parse():
@@ -67,7 +68,14 @@ def args_parse():
     p.add_argument("--design", default="filtered", choices=["filtered", "ridges"],
                    help="permittivity maps: filtered-threshold pixels or ridge edge positions")
     p.add_argument("--concurrent", type=int, default=8,
-                   help="independent designs in flight per GPU (one context + stream + host thread each)")
+                   help="independent designs in flight per GPU (one context each)")
+    p.add_argument("--mode", default="batch", choices=["batch", "streams"],
+                   help="batch: the designs share every launch (apf_solve_S_grad_batch, one stream); streams: one "
+                        "host thread + stream per design, one design per call")
+    p.add_argument("--no-compare", action="store_true", help="skip timing the other --mode for comparison")
+    p.add_argument("--planes", type=int, default=2, choices=[2, 3],
+                   help="bf16 split planes of the mixed elimination (3: bf16x6, for high-contrast slabs)")
+    p.add_argument("--butterfly", action="store_true", help="random butterfly transform of the slab blocks")
     return p.parse_args()
 
 
@@ -313,6 +321,8 @@ def main():
         sv.set_channels(None, None)
         if prec == "mixed":
             sv.set_refinement(a.refine_tol, 40)
+            if a.planes != 2 or a.butterfly:
+                sv.set_elimination(a.planes, a.butterfly)
         return sv
 
     solvers = [new_solver("mixed", x_host[b][0]) for b in range(B)]
@@ -371,39 +381,108 @@ def main():
         if errors:
             raise errors[0]
 
+    def step_batch_dev(i):
+        """One batched call: all B designs' S + grad f in shared launches."""
+        for b in range(B):
+            set_design(solvers[b], x_dev[b][i % nseeds])
+        apf.solve_S_grad_batch(solvers, "splitter", ORDERS, TARGET, out_S=S_d, out_grad=g_d)
+        if ridges:
+            for b in range(B):
+                solvers[b].ridge_grad(g_d[b], out=ge_d[b])
+
+    def step_batch_host(i):
+        for b in range(B):
+            set_design(solvers[b], x_host[b][i % nseeds])
+        if ridges:
+            apf.solve_S_grad_batch(solvers, "splitter", ORDERS, TARGET, out_grad=g_d)
+            for b in range(B):
+                solvers[b].ridge_grad(g_d[b])
+        else:
+            apf.solve_S_grad_batch(solvers, "splitter", ORDERS, TARGET)
+
+    def record_stats():
+        for b in range(B):
+            st = solvers[b].stats()
+            stats_acc[b]["launches"] += st["kernel_launches"]
+            stats_acc[b]["iters"].append(st["refine_iters"])
+            stats_acc[b]["fallbacks"] += st["leaf_fallbacks"]
+
+    def timed(run_steps, nsteps, sample_clocks=False):
+        """Device time of nsteps (events on the main stream, fenced against every
+        design's stream), max over ranks."""
+        master = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ends = [torch.cuda.Event() for _ in range(B)]
+        clk = Clocks(local) if sample_clocks else None
+        if clk:
+            clk.start()
+            time.sleep(0.3)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(master)
+        run_steps(nsteps, e0, ends)
+        for ev in ends:
+            master.wait_event(ev)
+        e1.record(master)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        return replicas.max_over_ranks(e0.elapsed_time(e1)), (clk.stop() if clk else None)
+
+    def batch_steps(nsteps, start_ev, end_evs, record=False):
+        with torch.cuda.stream(streams[0]):
+            streams[0].wait_event(start_ev)
+            for i in range(nsteps):
+                step_batch_dev(i)
+                if record:
+                    record_stats()
+            for ev in end_evs:
+                ev.record(streams[0])
+
+    def stream_steps(nsteps, start_ev, end_evs, record=False):
+        run_all(step_dev, nsteps, start_ev, end_evs, record=record)
+
+    batched = a.mode == "batch" and B > 1
     # ---- 1. the headline: B designs in flight, inputs resident on the device ----
-    run_all(step_dev, a.warmup)
-    torch.cuda.synchronize()
-    clk = Clocks(local)
-    master = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ends = [torch.cuda.Event() for _ in range(B)]
-    clk.start()
-    time.sleep(0.3)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0.record(master)
-    run_all(step_dev, a.steps, e0, ends, record=True)
-    for ev in ends:
-        master.wait_event(ev)
-    e1.record(master)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    clocks = clk.stop()
-    ms = replicas.max_over_ranks(e0.elapsed_time(e1))
+    if batched:
+        with torch.cuda.stream(streams[0]):
+            for i in range(a.warmup):
+                step_batch_dev(i)
+        ms, clocks = timed(lambda n, e, ev: batch_steps(n, e, ev, record=True), a.steps, sample_clocks=True)
+    else:
+        run_all(step_dev, a.warmup)
+        ms, clocks = timed(lambda n, e, ev: stream_steps(n, e, ev, record=True), a.steps, sample_clocks=True)
     value = replicas.whole_job_throughput(ws, B, a.steps, ms)
     launches = sum(x["launches"] for x in stats_acc)
     iters = stats_acc[0]["iters"]
     st_last = s.stats()
+    # the other way of keeping B designs in flight, for comparison
+    other = None
+    if B > 1 and not a.no_compare:
+        if batched:
+            run_all(step_dev, 1)
+            ms_o, _ = timed(lambda n, e, ev: stream_steps(n, e, ev), a.steps)
+            other = {"mode": f"{B} host threads, one context + stream each, one design per call",
+                     "value": replicas.whole_job_throughput(ws, B, a.steps, ms_o), "unit": "evals/s"}
+        else:
+            with torch.cuda.stream(streams[0]):
+                step_batch_dev(0)
+            ms_o, _ = timed(lambda n, e, ev: batch_steps(n, e, ev), a.steps)
+            other = {"mode": f"apf_solve_S_grad_batch, {B} designs per call", "unit": "evals/s",
+                     "value": replicas.whole_job_throughput(ws, B, a.steps, ms_o)}
 
     # ---- 2. end to end at the same concurrency and step count: host buffers ----
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     t0 = time.perf_counter()
-    run_all(step_host, a.steps)
+    if batched:
+        with torch.cuda.stream(streams[0]):
+            for i in range(a.steps):
+                step_batch_host(i)
+    else:
+        run_all(step_host, a.steps)
     torch.cuda.synchronize()
     t_e2e = replicas.max_over_ranks(time.perf_counter() - t0)
     e2e_val = ws * B * a.steps / t_e2e
@@ -415,26 +494,35 @@ def main():
         h2d = w.h * w.nx * 8
         d2h = nin * nout * 16 + w.h * w.nx * 8 + 8
 
-    # ---- 3. one design alone: its rate and the tensor-core GEMM's in-step roofline ----
+    # ---- 3. one design alone: its rate, then the tensor-core GEMM's in-step roofline ----
     # (a single stream, so every GEMM's CUDA-event interval is that launch alone)
+    n1 = max(3, a.steps // 2)
+
+    def one_design(nsteps, fn=None):
+        with torch.cuda.stream(streams[0]):
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(streams[0])
+            for i in range(nsteps):
+                (fn or step_dev)(0, i)
+            f1.record(streams[0])
+        torch.cuda.synchronize()
+        return f0.elapsed_time(f1) / nsteps
+
+    for i in range(2):
+        step_dev(0, i)
+    ms1 = one_design(n1)
     s.set_profiling(True)
     for i in range(2):
         step_dev(0, i)
     torch.cuda.synchronize()
     s.set_profiling(True)  # reset the counters, keep the captured graphs
-    n1 = max(3, a.steps // 2)
-    with torch.cuda.stream(streams[0]):
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(streams[0])
-        for i in range(n1):
-            step_dev(0, i)
-        f1.record(streams[0])
-    torch.cuda.synchronize()
-    ms1 = f0.elapsed_time(f1) / n1
+    ms1p = one_design(n1)
     prof = s.profile()
     s.set_profiling(False)
     single = {"value": 1000.0 / ms1, "unit": "evals/s", "steps": n1, "ms_per_step": ms1,
-              "gemm_ms_per_step": prof["gemm_ms"] / n1, "gemm_launches_per_step": prof["gemm_launches"] / n1}
+              "profiled_ms_per_step": ms1p, "gemm_ms_per_step": prof["gemm_ms"] / n1,
+              "gemm_launches_per_step": prof["gemm_launches"] / n1,
+              "launches_per_step": s.stats()["kernel_launches"]}
 
     # ---- 4. the float64 GPU path, the same design, one design at a time ----
     fp64 = None
@@ -555,7 +643,7 @@ def main():
                 "achieved_algorithmic_complex_tflops": alg_tf,
                 "note": (f"one design alone on one stream ({n1} steps): achieved = bf16 tensor flops (8 m n k per "
                          f"complex product x plane products) / summed CUDA-event launch time "
-                         f"({prof['gemm_ms'] / n1:.2f} ms of the {ms1:.2f} ms step); peak = bf16_tflops_sustained "
+                         f"({prof['gemm_ms'] / n1:.2f} ms of the {ms1p:.2f} ms profiled step); peak = bf16_tflops_sustained "
                          f"({src}, of measured); traffic = DRAM bytes per launch scaled from the ncu capture "
                          f"{GEMM_CAPTURE['profile']} by the launch's flops")}
     iso = isolated_gemm(apf, local, nin + nout, w.nx, w.nx)
@@ -592,13 +680,16 @@ def main():
                            "l2": f"working set {st_last['workspace_bytes'] / 1e9:.1f} GB per design > 129 MB L2, no flush",
                            "refine_iters": iters, "residual": st_last["residual"],
                            "leaf_fallbacks_per_step": sum(x["fallbacks"] for x in stats_acc) / (B * a.steps),
-                           "concurrent_designs_per_gpu": B,
+                           "concurrent_designs_per_gpu": B, "elimination_planes": a.planes,
+                           "butterfly": bool(a.butterfly),
+                           "mode": ("apf_solve_S_grad_batch: B designs share every launch" if batched else
+                                    "one host thread + stream per design"),
                            "parallelism": f"replicas x{ws}, {B} independent designs per GPU"},
                 "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "designs": B, "steps": a.steps,
                         "note": "same designs in flight and step count as value; wall clock incl. host copies"},
                 "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu,
-                "single_design": single, "fp64": fp64, "adjoint_method": adj, "schur_recompute": rec,
+                "single_design": single, "other_mode": other, "fp64": fp64, "adjoint_method": adj, "schur_recompute": rec,
                 "optimisation": opt,
                 "checks": checks, "concurrent_designs": B, "refine_tol": a.refine_tol,
                 "stages_ms": {k: st_last[k] for k in ("ms_boundary", "ms_eliminate", "ms_fields", "ms_readout",

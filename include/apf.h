@@ -164,6 +164,25 @@ int apf_solve_S_grad(apf_ctx *ctx, int objective, const double *params, int n_pa
 int apf_solve_S_grad_adjoint(apf_ctx *ctx, int objective, const double *params, int n_params,
                              double *S, double *f, double *grad_eps, void *stream);
 
+/* S, f and df/deps for nb independent designs in one call (nb <= 8; the
+   paper's Sec. 3 runs 1000 independent starts, and line searches try several
+   designs per iteration).  ctx[0..nb) are distinct contexts, each prepared
+   by apf_set_grid, apf_set_eps (its own permittivity) and apf_set_channels,
+   with the same grid, slab rows, channel orders, precision and refinement /
+   storage settings (APF_EINVAL otherwise).  In mixed mode every launch of the
+   slab elimination, the field sweeps and the gradient serves all nb designs
+   (so each launch has nb times the parallel work and there are about nb
+   times fewer launches per design); the refinement gives each design the
+   sweeps its own stopping rule asks for.  APF_FP64 contexts (and GMRES
+   refinement) are solved one after the other.  S[b] (may be NULL, or S
+   itself NULL), grad_eps[b] (not NULL) and f[b] (host, may be NULL) receive
+   design b's results as apf_solve_S_grad would; each context keeps its fields
+   for apf_grad_from_gamma.  One stream for all; synchronized before return.
+   Returns the first error of any design (APF_ENOCONV: all results
+   returned). */
+int apf_solve_S_grad_batch(apf_ctx *const *ctx, int nb, int objective, const double *params, int n_params,
+                           double *const *S, double *f, double *const *grad_eps, void *stream);
+
 /* df/deps = 2 Re sum_ba Gamma_ba dS_ba/deps for a caller-supplied
    Gamma = df/dS (n_out x n_in complex128), using the fields of the last
    solve (Eq. 1 with Eq. 3).  grad_eps: h*nx float64. */
@@ -264,6 +283,23 @@ int apf_get_stats(const apf_ctx *ctx, apf_stats *stats);
    not change.  Re-creates the workspace like apf_set_krylov (the fields of
    an earlier solve are gone).  APF_EINVAL in APF_FP64 mode for k != 0. */
 int apf_set_schur_storage(apf_ctx *ctx, int segment_rows);
+
+/* Mixed mode: accuracy of the low-precision slab elimination (the paper's
+   factorization, here an approximate one that float64 refinement corrects).
+   planes = 2 (default): every operand is split into two bf16 planes and three
+   plane products are summed (bf16x3, about 1e-5 relative per product);
+   planes = 3: three planes and six products (bf16x6, about 1e-7), twice the
+   tensor work of the elimination and 1.5 times the storage of the packed
+   inverses.  High-contrast slabs (e.g. silicon ridges in air) make the slab
+   Schur blocks ill-conditioned; their refinement can stall with two planes
+   and converges with three.  butterfly = 1 applies a symmetric random
+   butterfly transform (depth 2) to every slab block before its inversion
+   (G = U (U^T X U)^-1 U^T), which spreads the rows of strongly structured
+   blocks so that the recursion, which pivots only inside its 32 x 32 leaves,
+   meets no nearly singular leading block.  Re-creates the workspace like
+   apf_set_krylov.  APF_EINVAL for other values, or in APF_FP64 mode for
+   anything but (2, 0). */
+int apf_set_elimination(apf_ctx *ctx, int planes, int butterfly);
 
 /* Measurement support (no counterpart in the paper).  When enabled, every
    tensor-core GEMM launch of later solves is bracketed by CUDA events on the

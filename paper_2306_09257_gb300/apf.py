@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 from typing import Optional, Sequence
 
 import numpy as np
@@ -30,7 +31,8 @@ EXPORTS = ("apf_create", "apf_destroy", "apf_set_grid", "apf_set_eps", "apf_set_
            "apf_set_refinement", "apf_get_stats", "apf_set_profiling", "apf_get_profile",
            "apf_solve_S_noalloc", "apf_last_error", "apf_version", "apf_set_ridges", "apf_ridge_grad",
            "apf_substrate_orders", "apf_reflection", "apf_reverse_S", "apf_set_krylov",
-           "apf_solve_S_grad_adjoint", "apf_set_schur_storage",
+           "apf_solve_S_grad_adjoint", "apf_set_schur_storage", "apf_solve_S_grad_batch",
+           "apf_set_elimination",
            "apf_sno_create", "apf_sno_destroy", "apf_sno_num_params", "apf_sno_set_params",
            "apf_sno_get_params", "apf_sno_forward", "apf_sno_gradients", "apf_sno_train_step")
 
@@ -87,6 +89,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.apf_solve_S.argtypes = [vp, dp, vp]
     L.apf_solve_S_grad.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), i, dp, ctypes.POINTER(ctypes.c_double), dp, vp]
     L.apf_solve_S_grad_adjoint.argtypes = L.apf_solve_S_grad.argtypes
+    L.apf_solve_S_grad_batch.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(ctypes.c_double), i,
+                                         ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(vp), vp]
     L.apf_grad_from_gamma.argtypes = [vp, dp, dp, vp]
     L.apf_set_refinement.argtypes = [vp, d, i]
     L.apf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
@@ -96,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.apf_substrate_orders.argtypes = [vp, ip, ip]
     L.apf_set_krylov.argtypes = [vp, i]
     L.apf_set_schur_storage.argtypes = [vp, i]
+    L.apf_set_elimination.argtypes = [vp, i, i]
     L.apf_reflection.argtypes = [vp, ip, i, dp, vp]
     L.apf_reverse_S.argtypes = [vp, dp, vp]
     L.apf_set_ridges.argtypes = [vp, dp, i, i, d, d, i, i, d, d, dp, vp]
@@ -120,12 +125,19 @@ def _ptr(a, dtype) -> int:
     return a.data_ptr()
 
 
-def _stream_of(*arrays):
+def _stream_of(*arrays, device=None):
+    """The stream a call is ordered on: torch's current stream of the device
+    of the first CUDA tensor argument, else (when torch is in use and has
+    initialised CUDA) torch's current stream of `device`, else the legacy
+    default stream (None)."""
     for a in arrays:
         if a is not None and not isinstance(a, np.ndarray):
             import torch
             if isinstance(a, torch.Tensor) and a.is_cuda:
                 return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    torch = sys.modules.get("torch")
+    if device is not None and torch is not None and torch.cuda.is_initialized():
+        return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
     return None
 
 
@@ -171,7 +183,7 @@ class Solver:
             eps_slab = np.ascontiguousarray(eps_slab, dtype=np.float64)
         # a CUDA tensor is read in order on torch's current stream (after the ops that wrote it)
         self._check(self._L.apf_set_eps(self._h, _ptr(eps_slab, np.float64), int(j0), h,
-                                        float(eps_sub), float(eps_clad), _stream_of(eps_slab)))
+                                        float(eps_sub), float(eps_clad), _stream_of(eps_slab, device=self.device)))
         self.h = h
         self.version += 1
 
@@ -191,7 +203,7 @@ class Solver:
         self._check(self._L.apf_set_ridges(self._h, _ptr(edges, np.float64), int(edges.shape[0]),
                                            1 if mirror else 0, float(eps_ridge), float(eps_bg), int(j0), int(h),
                                            float(eps_sub), float(eps_clad), eps_p,
-                                           _stream_of(edges, eps if eps_out is not None else None)))
+                                           _stream_of(edges, eps if eps_out is not None else None, device=self.device)))
         self.h = int(h)
         self.n_edges = int(edges.shape[0])
         self.version += 1
@@ -202,7 +214,7 @@ class Solver:
         if isinstance(grad_eps, np.ndarray):
             grad_eps = np.ascontiguousarray(grad_eps, dtype=np.float64)
         g = np.empty(self.n_edges, dtype=np.float64) if out is None else out
-        st = _stream_of(grad_eps, g)
+        st = _stream_of(grad_eps, g, device=self.device)
         self._check(self._L.apf_ridge_grad(self._h, _ptr(grad_eps, np.float64), _ptr(g, np.float64), st))
         return g
 
@@ -240,7 +252,7 @@ class Solver:
         mi, _ = self.channels()
         R = np.empty((len(mr), len(mi)), dtype=np.complex128) if out is None else out
         arr = (ctypes.c_int * len(mr))(*[int(v) for v in mr])
-        st = _stream_of(R)
+        st = _stream_of(R, device=self.device)
         self._check(self._L.apf_reflection(self._h, arr, len(mr), _ptr(R, np.complex128), st))
         return R
 
@@ -250,7 +262,7 @@ class Solver:
         orders m_out."""
         mi, mo = self.channels()
         S = np.empty((len(mi), len(mo)), dtype=np.complex128) if out is None else out
-        st = _stream_of(S)
+        st = _stream_of(S, device=self.device)
         self._check(self._L.apf_reverse_S(self._h, _ptr(S, np.complex128), st))
         return S
 
@@ -264,6 +276,13 @@ class Solver:
         self._check(self._L.apf_set_schur_storage(self._h, int(segment_rows)))
         self.version += 1
 
+    def set_elimination(self, planes: int = 2, butterfly: bool = False):
+        """Mixed mode: bf16 split planes of the elimination (2: bf16x3, 3:
+        bf16x6) and the symmetric random butterfly transform of the slab
+        blocks (see apf_set_elimination)."""
+        self._check(self._L.apf_set_elimination(self._h, int(planes), 1 if butterfly else 0))
+        self.version += 1
+
     def set_krylov(self, m: int):
         """Mixed mode: GMRES(m) refinement (0: plain refinement); see apf_set_krylov."""
         self._check(self._L.apf_set_krylov(self._h, int(m)))
@@ -275,7 +294,7 @@ class Solver:
 
     def solve_S(self, out=None, allow_noconv=False):
         S = self._alloc_S() if out is None else out
-        st = _stream_of(S)
+        st = _stream_of(S, device=self.device)
         self.version += 1
         self._check(self._L.apf_solve_S(self._h, _ptr(S, np.complex128), st),
                     allow=(APF_ENOCONV,) if allow_noconv else ())
@@ -292,7 +311,7 @@ class Solver:
         g = np.empty((self.h, self.nx), dtype=np.float64) if out_grad is None else out_grad
         oid, params, npar = self.objective_params(kind, orders, target)
         f = ctypes.c_double()
-        st = _stream_of(S, g)
+        st = _stream_of(S, g, device=self.device)
         self.version += 1
         self._check(self._L.apf_solve_S_grad(self._h, oid, params, npar, _ptr(S, np.complex128),
                                              ctypes.byref(f), _ptr(g, np.float64), st),
@@ -308,7 +327,7 @@ class Solver:
         g = np.empty((self.h, self.nx), dtype=np.float64) if out_grad is None else out_grad
         oid, params, npar = self.objective_params(kind, orders, target)
         f = ctypes.c_double()
-        st = _stream_of(S, g)
+        st = _stream_of(S, g, device=self.device)
         self.version += 1
         self._check(self._L.apf_solve_S_grad_adjoint(self._h, oid, params, npar, _ptr(S, np.complex128),
                                                      ctypes.byref(f), _ptr(g, np.float64), st),
@@ -319,7 +338,7 @@ class Solver:
         g = np.empty((self.h, self.nx), dtype=np.float64) if out is None else out
         if isinstance(Gamma, np.ndarray):
             Gamma = np.ascontiguousarray(Gamma, dtype=np.complex128)
-        st = _stream_of(Gamma, g)
+        st = _stream_of(Gamma, g, device=self.device)
         self._check(self._L.apf_grad_from_gamma(self._h, _ptr(Gamma, np.complex128), _ptr(g, np.float64), st))
         return g
 
@@ -335,6 +354,30 @@ class Solver:
         s = Stats()
         self._check(self._L.apf_get_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+
+def solve_S_grad_batch(solvers: Sequence["Solver"], kind: str, orders: Sequence[int], target: float = 0.0,
+                       out_S=None, out_grad=None, allow_noconv=False):
+    """S, f and df/deps of several designs in one call (apf_solve_S_grad_batch):
+    `solvers` share grid, slab rows, channels and settings, each holding its
+    own permittivity.  Returns lists (S, f, grad) in solver order."""
+    nb = len(solvers)
+    L = solvers[0]._L
+    S = [sv._alloc_S() for sv in solvers] if out_S is None else list(out_S)
+    g = [np.empty((sv.h, sv.nx), dtype=np.float64) for sv in solvers] if out_grad is None else list(out_grad)
+    oid, params, npar = Solver.objective_params(kind, orders, target)
+    hs = (ctypes.c_void_p * nb)(*[sv._h.value for sv in solvers])
+    sp = (ctypes.c_void_p * nb)(*[_ptr(x, np.complex128) for x in S])
+    gp = (ctypes.c_void_p * nb)(*[_ptr(x, np.float64) for x in g])
+    f = (ctypes.c_double * nb)()
+    st = _stream_of(*S, *g, device=solvers[0].device)
+    for sv in solvers:
+        sv.version += 1
+    rc = L.apf_solve_S_grad_batch(hs, nb, oid, params, npar, sp, f, gp, st)
+    if rc != APF_OK and not (allow_noconv and rc == APF_ENOCONV):
+        msgs = [L.apf_last_error(sv._h).decode() for sv in solvers]
+        raise APFError(rc, "; ".join(m for m in msgs if m and m != "no error") or L.apf_last_error(None).decode())
+    return S, list(f), g
 
 
 def solver_for_workload(w, eps_slab, precision="fp64", device=0, m_in=None, m_out=None) -> Solver:

@@ -347,6 +347,21 @@ int apf_set_schur_storage(apf_ctx *c, int segment_rows) {
     return ensure_workspace(c);
 }
 
+int apf_set_elimination(apf_ctx *c, int planes, int butterfly) {
+    if (!c) return APF_EINVAL;
+    if (planes != 2 && planes != 3) return set_err(c, APF_EINVAL, "planes=%d must be 2 or 3", planes);
+    if (butterfly != 0 && butterfly != 1) return set_err(c, APF_EINVAL, "butterfly must be 0 or 1");
+    if (c->precision == APF_FP64 && (planes != 2 || butterfly))
+        return set_err(c, APF_EINVAL, "split planes and the butterfly transform apply to the mixed mode only");
+    if (planes == c->elim_planes && butterfly == c->butterfly) return APF_OK;
+    c->elim_planes = planes;
+    c->butterfly = butterfly;
+    if (c->ws_nx < 0) return APF_OK;  // allocated with the workspace at apf_set_channels
+    cudaSetDevice(c->device);
+    free_workspace(c);
+    return ensure_workspace(c);
+}
+
 int apf_set_profiling(apf_ctx *c, int enable) {
     if (!c) return APF_EINVAL;
     cudaSetDevice(c->device);
@@ -685,6 +700,130 @@ int apf_solve_S_grad_adjoint(apf_ctx *c, int objective, const double *params, in
     int r = finish(c, s, rc_solve);
     if (f) *f = fh;
     return r;
+}
+
+// Several designs in one call: the mixed pipeline with every launch of the
+// elimination, the field sweeps and the gradient shared by the designs.
+static bool same_problem(const apf_ctx *a, const apf_ctx *b) {
+    return a->device == b->device && a->precision == b->precision && a->nx == b->nx && a->ny == b->ny &&
+           a->npml_bot == b->npml_bot && a->npml_top == b->npml_top && a->lambda_px == b->lambda_px &&
+           a->R0 == b->R0 && a->power == b->power && a->h == b->h && a->j0 == b->j0 && a->eps_sub == b->eps_sub &&
+           a->eps_clad == b->eps_clad && a->m_in == b->m_in && a->m_out == b->m_out && a->ir_tol == b->ir_tol &&
+           a->ir_max == b->ir_max && a->krylov_m == b->krylov_m && a->schur_seg == b->schur_seg &&
+           a->butterfly == b->butterfly && a->elim_planes == b->elim_planes;
+}
+
+int apf_solve_S_grad_batch(apf_ctx *const *ctx, int nb, int objective, const double *params, int n_params,
+                           double *const *S, double *f, double *const *grad_eps, void *stream) {
+    if (!ctx || nb < 1 || nb > APF_MAX_BATCH || !grad_eps)
+        return set_err(nullptr, APF_EINVAL, "apf_solve_S_grad_batch: need 1..%d contexts and grad_eps", APF_MAX_BATCH);
+    for (int b = 0; b < nb; ++b) {
+        if (!ctx[b] || !grad_eps[b]) return set_err(nullptr, APF_EINVAL, "apf_solve_S_grad_batch: NULL entry %d", b);
+        for (int a = 0; a < b; ++a)
+            if (ctx[a] == ctx[b]) return set_err(ctx[b], APF_EINVAL, "a context appears twice in the batch");
+    }
+    apf_ctx *c0 = ctx[0];
+    for (int b = 0; b < nb; ++b) {
+        apf_ctx *c = ctx[b];
+        if (!c->grid_set || !c->eps_set || !c->ch_set || c->ws_nx < 0)
+            return set_err(c, APF_ESTATE, "solve needs apf_set_grid, apf_set_eps and apf_set_channels");
+        if (!same_problem(c0, c))
+            return set_err(c, APF_EINVAL, "batch entry %d: grid, slab rows, channels or settings differ from entry 0", b);
+    }
+    if (objective != APF_OBJ_POWER && objective != APF_OBJ_SPLITTER)
+        return set_err(c0, APF_EINVAL, "unknown objective id %d", objective);
+    if (!params || n_params < 2 || (int)params[1] < 1 || (int)params[1] > 16 || n_params != 2 + (int)params[1])
+        return set_err(c0, APF_EINVAL, "objective params must be {t, nD, d_1..d_nD} with 1 <= nD <= 16");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c0->precision == APF_FP64 || c0->krylov_m > 0) {
+        // float64 (SIMT products, already grid-filling) and GMRES refinement: one design at a time
+        for (int b = 0; b < nb; ++b) {
+            int rc = apf_solve_S_grad(ctx[b], objective, params, n_params, S ? S[b] : nullptr, f ? f + b : nullptr,
+                                      grad_eps[b], stream);
+            if (rc != APF_OK) return rc;
+        }
+        return APF_OK;
+    }
+    for (int b = 1; b < nb; ++b)
+        if (!mixed_batch_compatible(c0, ctx[b]))
+            return set_err(ctx[b], APF_EINVAL, "batch entry %d: mixed-mode workspace settings differ", b);
+    cudaSetDevice(c0->device);
+    for (int b = 0; b < nb; ++b) {
+        apf_ctx *c = ctx[b];
+        c->launches = 0;
+        c->prof_used = c->prof_static;
+        c->stats.refine_iters = 0;
+        c->stats.residual = 0.0;
+        c->fields_lay = -1;
+        set_layout(c, 0);
+        cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), s);
+    }
+    cudaEventRecord(c0->ev[0], s);
+    for (int b = 0; b < nb; ++b) launch_boundary(ctx[b], s);
+    cudaEventRecord(c0->ev[1], s);
+    int rc = mixed_eliminate_n(ctx, nb, s);
+    if (rc != APF_OK) { cudaStreamSynchronize(s); return rc; }
+    cudaEventRecord(c0->ev[2], s);
+    for (int b = 0; b < nb; ++b) {
+        apf_ctx *c = ctx[b];
+        launch_zero(c, c->d_Ew, sizeof(double2) * c->h * (long long)(c->cf + c->ca) * c->nx, s);
+        launch_build_rhs(c, c->d_Ew, s);
+    }
+    rc = mixed_fields_begin_n(ctx, nb, s);
+    if (rc != APF_OK) { cudaStreamSynchronize(s); return rc; }
+    int rcs[APF_MAX_BATCH] = {};
+    rc = mixed_refine_n(ctx, nb, s, rcs);
+    if (rc != APF_OK) { cudaStreamSynchronize(s); return rc; }
+    cudaEventRecord(c0->ev[3], s);
+    for (int b = 0; b < nb; ++b) {
+        launch_readout(ctx[b], s);
+        rc = launch_objective(ctx[b], objective, params, n_params, s);
+        if (rc != APF_OK) { cudaStreamSynchronize(s); return rc; }
+    }
+    cudaEventRecord(c0->ev[4], s);
+    rc = mixed_gradient_n(ctx, nb, s);
+    if (rc != APF_OK) { cudaStreamSynchronize(s); return rc; }
+    cudaEventRecord(c0->ev[5], s);
+    std::vector<double> fh(nb, 0.0);
+    std::vector<int> fl(2 * nb, 0);
+    for (int b = 0; b < nb; ++b) {
+        apf_ctx *c = ctx[b];
+        const size_t sb = sizeof(double2) * (size_t)c->nin * c->nout;
+        if (S && S[b]) cudaMemcpyAsync(S[b], c->d_S, sb, cudaMemcpyDefault, s);
+        cudaMemcpyAsync(grad_eps[b], c->d_grad, sizeof(double) * c->h * c->nx, cudaMemcpyDefault, s);
+        cudaMemcpyAsync(&fh[b], c->d_f, sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&fl[2 * b], c->d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return check_cuda(c0, e, "batched solve");
+    if (c0->prof_on) prof_collect(c0);
+    float ms[6] = {0};
+    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&ms[i], c0->ev[i], c0->ev[i + 1]);
+    float tot = 0;
+    cudaEventElapsedTime(&tot, c0->ev[0], c0->ev[5]);
+    int ret = APF_OK;
+    for (int b = 0; b < nb; ++b) {
+        apf_ctx *c = ctx[b];
+        c->stats.ms_boundary = ms[0];
+        c->stats.ms_eliminate = ms[1];
+        c->stats.ms_fields = ms[2];
+        c->stats.ms_readout = ms[3];
+        c->stats.ms_gradient = ms[4];
+        c->stats.ms_total = tot;
+        c->stats.kernel_launches = c->launches;
+        c->stats.leaf_fallbacks = fl[2 * b + 1];
+        c->fields_lay = 0;
+        if (f) f[b] = fh[b];
+        int r = APF_OK;
+        if (fl[2 * b] & FLAG_SINGULAR) r = set_err(c, APF_ESINGULAR, "zero pivot in a diagonal-block inversion");
+        else if (fl[2 * b] & FLAG_TIMEOUT) r = set_err(c, APF_ETIMEOUT, "a bounded device wait gave up");
+        else if (fl[2 * b] & FLAG_NONFINITE) r = set_err(c, APF_ECUDA, "non-finite value in the elimination");
+        else if (rcs[b] == APF_ENOCONV)
+            r = set_err(c, APF_ENOCONV, "refinement stopped at residual %.3e > tol %.3e", c->stats.residual, c->ir_tol);
+        if (r != APF_OK && (ret == APF_OK || ret == APF_ENOCONV)) ret = r;
+    }
+    return ret;
 }
 
 int apf_grad_from_gamma(apf_ctx *c, const double *Gamma, double *grad_eps, void *stream) {

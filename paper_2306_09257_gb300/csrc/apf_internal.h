@@ -82,6 +82,8 @@ struct apf_ctx {
     int ir_max = 40;
     int krylov_m = 0;  // mixed mode: GMRES(m) refinement when > 0
     int schur_seg = 0; // mixed mode: recompute the slab inverses in segments of this many rows (0: store all)
+    int butterfly = 0; // mixed mode: symmetric random butterfly transform of every slab block before inversion
+    int elim_planes = 2; // mixed mode: bf16 split planes of the elimination and sweep products (2: bf16x3, 3: bf16x6)
     // workspace signature
     int ws_nx = -1, ws_ny = -1, ws_h = -1, ws_min = -1, ws_mout = -1;
     long long ws_bytes = 0;
@@ -197,6 +199,13 @@ void mixed_free(apf_ctx *c);
 int mixed_eliminate(apf_ctx *c, cudaStream_t s);
 int mixed_fields_begin(apf_ctx *c, cudaStream_t s);
 int mixed_refine(apf_ctx *c, cudaStream_t s);
+// the same steps for a batch of designs (shared launches), see apf_solve_S_grad_batch
+constexpr int APF_MAX_BATCH = 8;
+int mixed_eliminate_n(apf_ctx *const *cs, int nb, cudaStream_t s);
+int mixed_fields_begin_n(apf_ctx *const *cs, int nb, cudaStream_t s);
+int mixed_refine_n(apf_ctx *const *cs, int nb, cudaStream_t s, int *rcs);
+int mixed_gradient_n(apf_ctx *const *cs, int nb, cudaStream_t s);
+bool mixed_batch_compatible(const apf_ctx *a, const apf_ctx *b);
 
 int set_err(apf_ctx *c, int code, const char *fmt, ...);
 void prof_collect(apf_ctx *c);

@@ -35,6 +35,11 @@ struct MixedWork {
     // segment's inverses are recomputed when a sweep needs them.
     int seg_rows = 0, nseg = 1, seg_loaded = -1;
     float *CK = nullptr;                             // (nseg - 1) checkpoints, 2 n^2 floats each
+    // Symmetric random butterfly transform of every slab block before its
+    // inversion (bfly = 1): X' = U^T X U, G = U X'^-1 U^T with a depth-2
+    // recursive butterfly U; BW holds its 2 n random diagonal entries.
+    int bfly = 0;
+    float *BW = nullptr;
     float *O32 = nullptr;                            // GEMM output planes, 2 * max(ncol, n_out) * nx
     double2 *r = nullptr, *delta = nullptr;          // refinement buffers (h*ncol*nx)
     double2 *cb = nullptr, *ct = nullptr;            // circulant products on the boundary rows
@@ -46,9 +51,19 @@ struct MixedWork {
     std::vector<void *> allocs;
 };
 
-int recompute_segment(apf_ctx *c, int seg, cudaStream_t s);
+namespace {
+struct Bat;
+}
+int recompute_segment_b(const Bat &bt, int seg, cudaStream_t s);
 
 namespace {
+
+// Per-design pointers of a batch of designs (entry blockIdx.z, or blockIdx.x
+// for the one-CTA-per-block leaf kernel); a single design uses entry 0.
+template <typename T>
+struct Tab {
+    T v[TC_MAX_BATCH];
+};
 
 __device__ __forceinline__ void split_bf16(float x, int nsplit, __nv_bfloat16 *o) {
     __nv_bfloat16 h0 = __float2bfloat16_rn(x);
@@ -73,12 +88,17 @@ struct PackJob {
     __nv_bfloat16 *out;
     long long kp, plane_pitch;
 };
-struct PackJobs {
-    PackJob j[2];
+// Up to N pack jobs per launch (blockIdx.z): the two operands of one product,
+// or those of the same product for every design of a batch.
+template <int N>
+struct PackJobsN {
+    PackJob j[N];
 };
+constexpr int MAX_JOBS = 2 * TC_MAX_BATCH;
 
 // Tile: 32 rows x 64 k; thread (tx, ty) handles k = k0 + 2 tx, +1 (bf16x2 stores).
-__global__ void __launch_bounds__(256) k_pack32(PackJobs jobs) {
+template <int N>
+__global__ void __launch_bounds__(256) k_pack32(PackJobsN<N> jobs) {
     const PackJob &J = jobs.j[blockIdx.z];
     __shared__ float tre[32][65], tim[32][65];
     const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
@@ -157,7 +177,8 @@ __device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (*v)[3], int p, bool 
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-__global__ void __launch_bounds__(256) k_pack32v(PackJobs jobs) {
+template <int N>
+__global__ void __launch_bounds__(256) k_pack32v(PackJobsN<N> jobs) {
     const PackJob &J = jobs.j[blockIdx.z];
     __shared__ float tre[32][65], tim[32][65];
     const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
@@ -207,11 +228,13 @@ __global__ void __launch_bounds__(256) k_pack32v(PackJobs jobs) {
 
 // A-layout pack of complex float64 rows (optionally the sum of two sources):
 // row r = [Re v(r,:), Im v(r,:)], v = s1 (+ s2).
-__global__ void k_pack64_A(const double2 *__restrict__ s1, const double2 *__restrict__ s2, long long ld, int R,
-                           int K, int nsplit, __nv_bfloat16 *out, long long kp, long long plane_pitch) {
+__global__ void k_pack64_A(Tab<const double2 *> s1t, Tab<const double2 *> s2t, long long ld, int R, int K,
+                           int nsplit, Tab<__nv_bfloat16 *> outt, long long kp, long long plane_pitch) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     int r = blockIdx.y;
     if (k >= K || r >= R) return;
+    const double2 *__restrict__ s1 = s1t.v[blockIdx.z], *__restrict__ s2 = s2t.v[blockIdx.z];
+    __nv_bfloat16 *out = outt.v[blockIdx.z];
     double2 v = s1[(long long)r * ld + k];
     if (s2) v = cadd(v, s2[(long long)r * ld + k]);
     __nv_bfloat16 sa[3], sb[3];
@@ -226,9 +249,11 @@ __global__ void k_pack64_A(const double2 *__restrict__ s1, const double2 *__rest
 
 // B-layout pack of the transpose of complex float64 rows: logical
 // v(r, k) = src[k][r] (r < R, k < K) -> rows r and R + r.
-__global__ void k_pack64_BT(const double2 *__restrict__ src, long long ld, int R, int K, int nsplit,
-                            __nv_bfloat16 *out, long long kp, long long plane_pitch) {
+__global__ void k_pack64_BT(Tab<const double2 *> srct, long long ld, int R, int K, int nsplit,
+                            Tab<__nv_bfloat16 *> outt, long long kp, long long plane_pitch) {
     __shared__ double2 t[32][33];
+    const double2 *__restrict__ src = srct.v[blockIdx.z];
+    __nv_bfloat16 *out = outt.v[blockIdx.z];
     int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
     int tx = threadIdx.x, ty = threadIdx.y;
     for (int i = ty; i < 32; i += 8) {
@@ -260,8 +285,12 @@ __global__ void k_pack64_BT(const double2 *__restrict__ src, long long ld, int R
 // X_j = K_j - G_{j-1} in float32 planes (K_j: 4 - k^2 eps on the diagonal,
 // -1 on the periodic neighbours, the circulants Sigma_bot / Sigma_top on the
 // first / last slab row).  Thread: 4 consecutive columns xp of row x (n % 4 == 0).
-__global__ void k_assemble32(GridDev g, int row, const double *eps, const double2 *circ, const float *Gre,
-                             const float *Gim, float *Xre, float *Xim) {
+__global__ void k_assemble32(GridDev g, int row, Tab<const double *> epst, const double2 *circ,
+                             Tab<const float *> Gret, Tab<const float *> Gimt, Tab<float *> Xret, Tab<float *> Ximt) {
+    const int b = blockIdx.z;
+    const double *eps = epst.v[b];
+    const float *Gre = Gret.v[b], *Gim = Gimt.v[b];
+    float *Xre = Xret.v[b], *Xim = Ximt.v[b];
     const int n = g.nx;
     const int x = blockIdx.y;
     const int xp0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -290,6 +319,83 @@ __global__ void k_assemble32(GridDev g, int row, const double *eps, const double
     }
     *reinterpret_cast<float4 *>(Xre + idx) = make_float4(vr[0], vr[1], vr[2], vr[3]);
     *reinterpret_cast<float4 *>(Xim + idx) = make_float4(vi[0], vi[1], vi[2], vi[3]);
+}
+
+// Symmetric random butterfly transform (depth 2) of an n x n complex-symmetric
+// block in planar float32, in place.  U = P Q with Q the n-point butterfly
+// (1/sqrt2)[R0 R1; R0 -R1] and P = diag of two n/2-point butterflies, R* random
+// diagonals near 1; such a two-sided transform spreads every row over rows
+// n/4 apart, so that the leading blocks of the Schur recursion (which pivots
+// only inside its 32 x 32 leaves) are not the nearly singular sub-blocks of a
+// strongly structured slab (high-contrast ridges) -- the randomisation that
+// lets symmetric indefinite elimination run without pivoting.
+//   forward: X' = U^T X U   (rows and columns: P^T then Q^T);
+//   inverse: G  = U Y U^T   (rows and columns: Q then P).
+// w[0 .. n): level-Q diagonals (R0 at i, R1 at n/2 + i); w[n .. 2n): level-P,
+// half h (0 / 1) at n + h n/2 (R0 at i, R1 at n/4 + i).  One thread per 4 x 4
+// group of rows {i, i+n/4, i+n/2, i+3n/4} x columns {j, ...}, i, j < n/4.
+__device__ __forceinline__ void bf_fwd(float2 &t, float2 &b, float wa, float wb) {
+    const float c = 0.70710678118654752f;
+    const float2 s = make_float2(t.x + b.x, t.y + b.y), d = make_float2(t.x - b.x, t.y - b.y);
+    t = make_float2(c * wa * s.x, c * wa * s.y);
+    b = make_float2(c * wb * d.x, c * wb * d.y);
+}
+__device__ __forceinline__ void bf_inv(float2 &t, float2 &b, float wa, float wb) {
+    const float c = 0.70710678118654752f;
+    const float2 u = make_float2(wa * t.x, wa * t.y), v = make_float2(wb * b.x, wb * b.y);
+    t = make_float2(c * (u.x + v.x), c * (u.y + v.y));
+    b = make_float2(c * (u.x - v.x), c * (u.y - v.y));
+}
+template <bool INV>
+__global__ void k_butterfly(Tab<float *> ret, Tab<float *> imt, long long ld, int n, const float *w) {
+    float *re = ret.v[blockIdx.z], *im = imt.v[blockIdx.z];
+    const int q = n >> 2;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (j >= q || i >= q) return;
+    float2 m[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const long long g = (long long)(i + r * q) * ld + (j + c * q);
+            m[r][c] = make_float2(re[g], im[g]);
+        }
+    // P level pairs (0,1) [half 0] and (2,3) [half 1] at local index i / j;
+    // Q level pairs (0,2) and (1,3) at index i, i + q (resp. j, j + q)
+    auto rows = [&](int a, int b, float wa, float wb) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (INV) bf_inv(m[a][c], m[b][c], wa, wb);
+            else bf_fwd(m[a][c], m[b][c], wa, wb);
+        }
+    };
+    auto cols = [&](int a, int b, float wa, float wb) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (INV) bf_inv(m[r][a], m[r][b], wa, wb);
+            else bf_fwd(m[r][a], m[r][b], wa, wb);
+        }
+    };
+    const float *wq = w, *wp0 = w + n, *wp1 = w + n + n / 2;
+    if (!INV) {
+        rows(0, 1, wp0[i], wp0[q + i]); rows(2, 3, wp1[i], wp1[q + i]);
+        rows(0, 2, wq[i], wq[2 * q + i]); rows(1, 3, wq[q + i], wq[3 * q + i]);
+        cols(0, 1, wp0[j], wp0[q + j]); cols(2, 3, wp1[j], wp1[q + j]);
+        cols(0, 2, wq[j], wq[2 * q + j]); cols(1, 3, wq[q + j], wq[3 * q + j]);
+    } else {
+        rows(0, 2, wq[i], wq[2 * q + i]); rows(1, 3, wq[q + i], wq[3 * q + i]);
+        rows(0, 1, wp0[i], wp0[q + i]); rows(2, 3, wp1[i], wp1[q + i]);
+        cols(0, 2, wq[j], wq[2 * q + j]); cols(1, 3, wq[q + j], wq[3 * q + j]);
+        cols(0, 1, wp0[j], wp0[q + j]); cols(2, 3, wp1[j], wp1[q + j]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const long long g = (long long)(i + r * q) * ld + (j + c * q);
+            re[g] = m[r][c].x;
+            im[g] = m[r][c].y;
+        }
 }
 
 // Float32 Gauss-Jordan inverse of an n x n (n <= 128) diagonal block with
@@ -389,8 +495,9 @@ __global__ void __launch_bounds__(NB * 4) k_leaf32r(float *re, float *im, long l
     leaf_gj_regs<NB>(re, im, ld, flags);
 }
 
-__global__ void __launch_bounds__(512) k_leaf128rec(float *re, float *im, long long ld, int *flags) {
-    leaf128_recursive(re, im, ld, flags);
+__global__ void __launch_bounds__(512) k_leaf128rec(Tab<float *> re, Tab<float *> im, long long ld, Tab<int *> flags) {
+    const int b = blockIdx.x;
+    leaf128_recursive(re.v[b], im.v[b], ld, flags.v[b]);
 }
 
 template <int NB>
@@ -399,9 +506,12 @@ __global__ void __launch_bounds__(NB * 4) k_leaf32r2(float *re, float *im, long 
 }
 
 // C block <- -V, B block <- -V^T (planar float32).
-__global__ void k_negoff32(float *Bre, float *Bim, float *Cre, float *Cim, long long ld, const float *Vre,
-                           const float *Vim, int h) {
+__global__ void k_negoff32(Tab<float *> Bret, Tab<float *> Bimt, Tab<float *> Cret, Tab<float *> Cimt, long long ld,
+                           Tab<const float *> Vret, Tab<const float *> Vimt, int h) {
     __shared__ float tr[32][33], ti[32][33];
+    const int b = blockIdx.z;
+    float *Bre = Bret.v[b], *Bim = Bimt.v[b], *Cre = Cret.v[b], *Cim = Cimt.v[b];
+    const float *Vre = Vret.v[b], *Vim = Vimt.v[b];
     int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
     int tx = threadIdx.x, ty = threadIdx.y;
     for (int i = ty; i < 32; i += 8) {
@@ -424,11 +534,15 @@ __global__ void k_negoff32(float *Bre, float *Bim, float *Cre, float *Cim, long 
 }
 
 // E[c][x] = (R ? R[c][x] : 0) + O[c][x] for c < mcols;  E = R for c >= mcols.
-__global__ void k_combine(double2 *E, const double2 *R, const float *Ore, const float *Oim, int ncol, int mcols,
-                          int nx) {
+__global__ void k_combine(Tab<double2 *> Et, Tab<const double2 *> Rt, Tab<const float *> Oret,
+                          Tab<const float *> Oimt, int ncol, int mcols, int nx) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
     if (x >= nx) return;
+    const int b = blockIdx.z;
+    double2 *E = Et.v[b];
+    const double2 *R = Rt.v[b];
+    const float *Ore = Oret.v[b], *Oim = Oimt.v[b];
     long long i = (long long)c * nx + x;
     double2 v = R ? R[i] : cmk(0, 0);
     if (c < mcols) { v.x += (double)Ore[i]; v.y += (double)Oim[i]; }
@@ -560,9 +674,13 @@ __global__ void k_axpy(double2 *E, const double2 *d, long long n) {
 // g_j(x) = 2 k^2 Re sum_b Phi_j[b][x] Q[b][x].  Block: 32 consecutive x (lanes)
 // x 8 warps, warp w summing b = w, w + 8, ...; the 8 partial sums are added in
 // a fixed order (deterministic).
-__global__ void __launch_bounds__(256) k_grad_rowdot32(const double2 *E, const float *Qre, const float *Qim, int j,
-                                                       int nx, int n_in, int n_out, double k2, double *g) {
+__global__ void __launch_bounds__(256) k_grad_rowdot32(Tab<const double2 *> Et, Tab<const float *> Qret,
+                                                       Tab<const float *> Qimt, int j, int nx, int n_in, int n_out,
+                                                       double k2, Tab<double *> gt) {
     __shared__ double part[8][32];
+    const double2 *E = Et.v[blockIdx.z];
+    const float *Qre = Qret.v[blockIdx.z], *Qim = Qimt.v[blockIdx.z];
+    double *g = gt.v[blockIdx.z];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int x = blockIdx.x * 32 + lane;
     const int ncol = n_in + n_out;
@@ -617,8 +735,9 @@ PackJob make_job(__nv_bfloat16 *dst, const PV &src, int R, int K, bool trans, bo
     return PackJob{src.re, src.im, src.ld, R, K, trans ? 1 : 0, layoutB ? 1 : 0, nsplit, dst, kp, rows * kp};
 }
 
-void launch_jobs(apf_ctx *c, const PackJob *js, int nj, cudaStream_t s) {
-    PackJobs jobs{};
+template <int N>
+void launch_jobs_n(apf_ctx *c, const PackJob *js, int nj, cudaStream_t s) {
+    PackJobsN<N> jobs{};
     int maxR = 0, maxK = 0;
     for (int i = 0; i < nj; ++i) {
         jobs.j[i] = js[i];
@@ -635,8 +754,13 @@ void launch_jobs(apf_ctx *c, const PackJob *js, int nj, cudaStream_t s) {
               ((((uintptr_t)J.re) | ((uintptr_t)J.im) | ((uintptr_t)J.out)) & 15) == 0 && J.kp % 8 == 0 &&
               J.plane_pitch % 8 == 0;
     }
-    if (vec) APF_LAUNCH(c, k_pack32v, grid, 256, 0, s, jobs);
-    else APF_LAUNCH(c, k_pack32, grid, dim3(32, 8), 0, s, jobs);
+    if (vec) APF_LAUNCH(c, k_pack32v<N>, grid, 256, 0, s, jobs);
+    else APF_LAUNCH(c, k_pack32<N>, grid, dim3(32, 8), 0, s, jobs);
+}
+
+void launch_jobs(apf_ctx *c, const PackJob *js, int nj, cudaStream_t s) {
+    if (nj <= 2) launch_jobs_n<2>(c, js, nj, s);
+    else launch_jobs_n<MAX_JOBS>(c, js, nj, s);
 }
 
 PackView pack32(apf_ctx *c, __nv_bfloat16 *dst, const PV &src, int R, int K, bool trans, bool layoutB, int nsplit,
@@ -647,89 +771,176 @@ PackView pack32(apf_ctx *c, __nv_bfloat16 *dst, const PV &src, int R, int K, boo
     return v;
 }
 
-// Pack the A and B operands of one product in a single launch.
-void pack2(apf_ctx *c, PackView *va, __nv_bfloat16 *da, const PV &sa, int Ra, int Ka, bool ta, PackView *vb,
-           __nv_bfloat16 *db, const PV &sb, int Rb, int Kb, bool tb, int nsplit, cudaStream_t s) {
-    PackJob js[2] = {make_job(da, sa, Ra, Ka, ta, false, nsplit, va), make_job(db, sb, Rb, Kb, tb, true, nsplit, vb)};
-    launch_jobs(c, js, 2, s);
+// The designs of one call: every step below launches once for all of them
+// (they share grid, slab height, channel set and settings; each has its own
+// buffers).  A single design is a batch of one.
+struct Bat {
+    int n = 1;
+    apf_ctx *c[TC_MAX_BATCH] = {};
+    apf_ctx *lead() const { return c[0]; }
+};
+
+Bat one(apf_ctx *c) {
+    Bat b;
+    b.n = 1;
+    b.c[0] = c;
+    return b;
 }
 
-PackView pack64A(apf_ctx *c, __nv_bfloat16 *dst, const double2 *s1, const double2 *s2, long long ld, int R, int K,
-                 int nsplit, cudaStream_t s) {
-    long long kp = round_up(2LL * K, 64);
-    if (kp != 2LL * K) cudaMemsetAsync(dst, 0, sizeof(__nv_bfloat16) * R * kp * nsplit, s);
-    dim3 grid((K + 255) / 256, R);
-    APF_LAUNCH(c, k_pack64_A, grid, 256, 0, s, s1, s2, ld, R, K, nsplit, dst, kp, (long long)R * kp);
-    return PackView{dst, R, kp, nsplit, (long long)R * kp};
+template <typename T, typename F>
+Tab<T> tab(const Bat &bt, F f) {
+    Tab<T> t{};
+    for (int b = 0; b < bt.n; ++b) t.v[b] = f(b);
+    return t;
 }
 
-PackView pack64BT(apf_ctx *c, __nv_bfloat16 *dst, const double2 *src, long long ld, int R, int K, int nsplit,
-                  cudaStream_t s) {
-    long long kp = round_up(2LL * K, 64);
-    long long rows = 2LL * R;
-    if (kp != 2LL * K) cudaMemsetAsync(dst, 0, sizeof(__nv_bfloat16) * rows * kp * nsplit, s);
-    dim3 grid((K + 31) / 32, (R + 31) / 32);
-    APF_LAUNCH(c, k_pack64_BT, grid, dim3(32, 8), 0, s, src, ld, R, K, nsplit, dst, kp, rows * kp);
-    return PackView{dst, rows, kp, nsplit, rows * kp};
+// Pack the A operand sa[b] and the B operand sb[b] of one product for every
+// design (in w->PA / w->PB of each design) in one launch.
+void pack2_b(const Bat &bt, PackView *va, const PV *sa, int Ra, int Ka, bool ta, PackView *vb, const PV *sb, int Rb,
+             int Kb, bool tb, int nsplit, cudaStream_t s) {
+    PackJob js[2 * TC_MAX_BATCH];
+    for (int b = 0; b < bt.n; ++b) {
+        MixedWork *w = bt.c[b]->mw;
+        js[2 * b] = make_job(w->PA, sa[b], Ra, Ka, ta, false, nsplit, &va[b]);
+        js[2 * b + 1] = make_job(w->PB, sb[b], Rb, Kb, tb, true, nsplit, &vb[b]);
+    }
+    launch_jobs(bt.lead(), js, 2 * bt.n, s);
+}
+
+void pack32_b(const Bat &bt, PackView *v, __nv_bfloat16 *const *dst, const PV *src, int R, int K, bool trans,
+              bool layoutB, int nsplit, cudaStream_t s) {
+    PackJob js[TC_MAX_BATCH];
+    for (int b = 0; b < bt.n; ++b) js[b] = make_job(dst[b], src[b], R, K, trans, layoutB, nsplit, &v[b]);
+    launch_jobs(bt.lead(), js, bt.n, s);
+}
+
+void pack64A_b(const Bat &bt, PackView *v, __nv_bfloat16 *const *dst, const double2 *const *s1,
+               const double2 *const *s2, long long ld, int R, int K, int nsplit, cudaStream_t s) {
+    const long long kp = round_up(2LL * K, 64);
+    for (int b = 0; b < bt.n; ++b) {
+        if (kp != 2LL * K) cudaMemsetAsync(dst[b], 0, sizeof(__nv_bfloat16) * R * kp * nsplit, s);
+        v[b] = PackView{dst[b], R, kp, nsplit, (long long)R * kp};
+    }
+    dim3 grid((K + 255) / 256, R, bt.n);
+    APF_LAUNCH(bt.lead(), k_pack64_A, grid, 256, 0, s, tab<const double2 *>(bt, [&](int b) { return s1[b]; }),
+               tab<const double2 *>(bt, [&](int b) { return s2 ? s2[b] : nullptr; }), ld, R, K, nsplit,
+               tab<__nv_bfloat16 *>(bt, [&](int b) { return dst[b]; }), kp, (long long)R * kp);
+}
+
+void pack64BT_b(const Bat &bt, PackView *v, __nv_bfloat16 *const *dst, const double2 *const *src, long long ld, int R,
+                int K, int nsplit, cudaStream_t s) {
+    const long long kp = round_up(2LL * K, 64);
+    const long long rows = 2LL * R;
+    for (int b = 0; b < bt.n; ++b) {
+        if (kp != 2LL * K) cudaMemsetAsync(dst[b], 0, sizeof(__nv_bfloat16) * rows * kp * nsplit, s);
+        v[b] = PackView{dst[b], rows, kp, nsplit, rows * kp};
+    }
+    dim3 grid((K + 31) / 32, (R + 31) / 32, bt.n);
+    APF_LAUNCH(bt.lead(), k_pack64_BT, grid, dim3(32, 8), 0, s,
+               tab<const double2 *>(bt, [&](int b) { return src[b]; }), ld, R, K, nsplit,
+               tab<__nv_bfloat16 *>(bt, [&](int b) { return dst[b]; }), kp, rows * kp);
+}
+
+// out[b] = alpha A[b] B[b]^T + beta in[b] for every design, one launch.
+int gemm_b(const Bat &bt, const PackView *A, const PackView *B, int nsplit, int M, int N, int n_cplx, float alpha,
+           float beta, const PV *out, const PV *in, cudaStream_t s) {
+    TcProblem pb[TC_MAX_BATCH];
+    for (int b = 0; b < bt.n; ++b)
+        pb[b] = TcProblem{A[b], B[b], out[b].re, out[b].im, in ? in[b].re : nullptr, in ? in[b].im : nullptr,
+                          bt.c[b]->d_flags};
+    return tc_gemm_n(bt.lead(), bt.n, pb, nsplit, M, N, n_cplx, alpha, beta, out[0].ld, in ? in[0].ld : 0, s);
 }
 
 int leaf_size(const MixedWork *w) { return w->leaf; }
 
-// X <- X^-1 in place for complex-symmetric X, the 2x2 block Schur recursion of
-// the float64 path with all four products on the tensor cores.
-int inv32(apf_ctx *c, const PV &X, int n, float *Tre, float *Tim, float *Vre, float *Vim, cudaStream_t s) {
+// Diagonal block of the recursion, one design (kernel variant per the context's knobs).
+void leaf_one(apf_ctx *lead, const PV &X, int n, int *flags, cudaStream_t s) {
+    MixedWork *w = lead->mw;
+    Tab<float *> re{}, im{};
+    Tab<int *> fl{};
+    re.v[0] = X.re; im.v[0] = X.im; fl.v[0] = flags;
+    // 128 blocks: in-CTA Schur recursion over 32 x 32 Gauss-Jordan leaves
+    // (default); variants 1-3 are the single-level Gauss-Jordan kernels.
+    if (n == 128 && w->leaf_variant == 1)
+        APF_LAUNCH(lead, k_leaf32r2<128>, 1, 512, 0, s, X.re, X.im, X.ld, flags);
+    else if (n == 128 && w->leaf_variant == 2)
+        APF_LAUNCH(lead, k_leaf32<128>, 1, 512, leaf_smem_bytes<128>(8), s, X.re, X.im, X.ld, flags);
+    else if (n == 128 && w->leaf_variant == 3)
+        APF_LAUNCH(lead, k_leaf32r<128>, 1, 512, 0, s, X.re, X.im, X.ld, flags);
+    else if (n == 128)
+        APF_LAUNCH(lead, k_leaf128rec, 1, 512, rec_smem_bytes(), s, re, im, X.ld, fl);
+    else if (n == 64 && w->leaf_variant == 1)
+        APF_LAUNCH(lead, k_leaf32r2<64>, 1, 256, 0, s, X.re, X.im, X.ld, flags);
+    else if (n == 64)
+        APF_LAUNCH(lead, k_leaf32r<64>, 1, 256, 0, s, X.re, X.im, X.ld, flags);
+    else if (n == 32)
+        APF_LAUNCH(lead, k_leaf32<32>, 1, 128, leaf_smem_bytes<32>(8), s, X.re, X.im, X.ld, flags);
+    else if (n == 16)
+        APF_LAUNCH(lead, k_leaf32<16>, 1, 64, leaf_smem_bytes<16>(8), s, X.re, X.im, X.ld, flags);
+    else
+        APF_LAUNCH(lead, k_leaf_inv32, 1, 256, n * n * (int)sizeof(float2), s, X.re, X.im, X.ld, n, flags);
+}
+
+// X[b] <- X[b]^-1 in place for complex-symmetric X[b], every design of the
+// batch: the 2x2 block Schur recursion of the float64 path with all four
+// products on the tensor cores.
+int inv32_b(const Bat &bt, const PV *X, int n, float *const *Tre, float *const *Tim, float *const *Vre,
+            float *const *Vim, cudaStream_t s) {
+    apf_ctx *c = bt.lead();
     MixedWork *w = c->mw;
+    const int nb = bt.n;
     if (n <= leaf_size(w)) {
-        // 128 blocks: in-CTA Schur recursion over 32 x 32 Gauss-Jordan leaves
-        // (default); variants 1-3 are the single-level Gauss-Jordan kernels.
-        if (n == 128 && w->leaf_variant == 1)
-            APF_LAUNCH(c, k_leaf32r2<128>, 1, 512, 0, s, X.re, X.im, X.ld, c->d_flags);
-        else if (n == 128 && w->leaf_variant == 2)
-            APF_LAUNCH(c, k_leaf32<128>, 1, 512, leaf_smem_bytes<128>(8), s, X.re, X.im, X.ld, c->d_flags);
-        else if (n == 128 && w->leaf_variant == 3)
-            APF_LAUNCH(c, k_leaf32r<128>, 1, 512, 0, s, X.re, X.im, X.ld, c->d_flags);
-        else if (n == 128)
-            APF_LAUNCH(c, k_leaf128rec, 1, 512, rec_smem_bytes(), s, X.re, X.im, X.ld, c->d_flags);
-        else if (n == 64 && w->leaf_variant == 1)
-            APF_LAUNCH(c, k_leaf32r2<64>, 1, 256, 0, s, X.re, X.im, X.ld, c->d_flags);
-        else if (n == 64)
-            APF_LAUNCH(c, k_leaf32r<64>, 1, 256, 0, s, X.re, X.im, X.ld, c->d_flags);
-        else if (n == 32)
-            APF_LAUNCH(c, k_leaf32<32>, 1, 128, leaf_smem_bytes<32>(8), s, X.re, X.im, X.ld, c->d_flags);
-        else if (n == 16)
-            APF_LAUNCH(c, k_leaf32<16>, 1, 64, leaf_smem_bytes<16>(8), s, X.re, X.im, X.ld, c->d_flags);
-        else
-            APF_LAUNCH(c, k_leaf_inv32, 1, 256, n * n * (int)sizeof(float2), s, X.re, X.im, X.ld, n, c->d_flags);
+        if (n == 128 && w->leaf_variant == 0) {
+            // one CTA per design's block
+            APF_LAUNCH(c, k_leaf128rec, nb, 512, rec_smem_bytes(), s, tab<float *>(bt, [&](int b) { return X[b].re; }),
+                       tab<float *>(bt, [&](int b) { return X[b].im; }), X[0].ld,
+                       tab<int *>(bt, [&](int b) { return bt.c[b]->d_flags; }));
+        } else {
+            for (int b = 0; b < nb; ++b) leaf_one(c, X[b], n, bt.c[b]->d_flags, s);
+        }
         return APF_OK;
     }
-    int h = n / 2;
-    int ns = w->nsplit_elim;
-    PV A = X, B = X.off(0, h), C = X.off(h, 0), D = X.off(h, h);
-    PV T{Tre, Tim, h}, V{Vre, Vim, h};
-    long long hh = (long long)h * h;
+    const int h = n / 2;
+    const int ns = w->nsplit_elim;
+    const long long hh = (long long)h * h;
+    PV A[TC_MAX_BATCH], B[TC_MAX_BATCH], C[TC_MAX_BATCH], D[TC_MAX_BATCH], T[TC_MAX_BATCH], V[TC_MAX_BATCH];
+    float *tr2[TC_MAX_BATCH], *ti2[TC_MAX_BATCH], *vr2[TC_MAX_BATCH], *vi2[TC_MAX_BATCH];
+    for (int b = 0; b < nb; ++b) {
+        A[b] = X[b]; B[b] = X[b].off(0, h); C[b] = X[b].off(h, 0); D[b] = X[b].off(h, h);
+        T[b] = PV{Tre[b], Tim[b], h}; V[b] = PV{Vre[b], Vim[b], h};
+        tr2[b] = Tre[b] + hh; ti2[b] = Tim[b] + hh; vr2[b] = Vre[b] + hh; vi2[b] = Vim[b] + hh;
+    }
     int rc;
-    if ((rc = inv32(c, A, h, Tre + hh, Tim + hh, Vre + hh, Vim + hh, s))) return rc;
+    PackView pa[TC_MAX_BATCH], pb[TC_MAX_BATCH];
+    if ((rc = inv32_b(bt, A, h, tr2, ti2, vr2, vi2, s))) return rc;
     // T = C Ai
-    PackView pa, pb;
-    pack2(c, &pa, w->PA, C, h, h, false, &pb, w->PB, A, h, h, false, ns, s);
-    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, 1.f, 0.f, T.re, T.im, T.ld, nullptr, nullptr, 0, s))) return rc;
+    pack2_b(bt, pa, C, h, h, false, pb, A, h, h, false, ns, s);
+    if ((rc = gemm_b(bt, pa, pb, ns, h, 2 * h, h, 1.f, 0.f, T, nullptr, s))) return rc;
     // D = D - T B   (B-operand columns = rows of C)
-    pack2(c, &pa, w->PA, T, h, h, false, &pb, w->PB, C, h, h, false, ns, s);
-    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, -1.f, 1.f, D.re, D.im, D.ld, D.re, D.im, D.ld, s))) return rc;
-    if ((rc = inv32(c, D, h, Tre + hh, Tim + hh, Vre + hh, Vim + hh, s))) return rc;
+    pack2_b(bt, pa, T, h, h, false, pb, C, h, h, false, ns, s);
+    if ((rc = gemm_b(bt, pa, pb, ns, h, 2 * h, h, -1.f, 1.f, D, D, s))) return rc;
+    if ((rc = inv32_b(bt, D, h, tr2, ti2, vr2, vi2, s))) return rc;
     // V = Si T
-    pack2(c, &pa, w->PA, D, h, h, false, &pb, w->PB, T, h, h, true, ns, s);
-    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, 1.f, 0.f, V.re, V.im, V.ld, nullptr, nullptr, 0, s))) return rc;
-    // A = Ai + V^T T
-    pa = pack32(c, w->PA, V, h, h, true, false, ns, s);
-    if ((rc = tc_gemm(c, pa, pb, ns, h, 2 * h, h, 1.f, 1.f, A.re, A.im, A.ld, A.re, A.im, A.ld, s))) return rc;
-    dim3 grid((h + 31) / 32, (h + 31) / 32);
-    APF_LAUNCH(c, k_negoff32, grid, dim3(32, 8), 0, s, B.re, B.im, C.re, C.im, X.ld, V.re, V.im, h);
+    pack2_b(bt, pa, D, h, h, false, pb, T, h, h, true, ns, s);
+    if ((rc = gemm_b(bt, pa, pb, ns, h, 2 * h, h, 1.f, 0.f, V, nullptr, s))) return rc;
+    // A = Ai + V^T T   (the B operand is still the packed T^T)
+    __nv_bfloat16 *padst[TC_MAX_BATCH];
+    for (int b = 0; b < nb; ++b) padst[b] = bt.c[b]->mw->PA;
+    pack32_b(bt, pa, padst, V, h, h, true, false, ns, s);
+    if ((rc = gemm_b(bt, pa, pb, ns, h, 2 * h, h, 1.f, 1.f, A, A, s))) return rc;
+    dim3 grid((h + 31) / 32, (h + 31) / 32, nb);
+    APF_LAUNCH(c, k_negoff32, grid, dim3(32, 8), 0, s, tab<float *>(bt, [&](int b) { return B[b].re; }),
+               tab<float *>(bt, [&](int b) { return B[b].im; }), tab<float *>(bt, [&](int b) { return C[b].re; }),
+               tab<float *>(bt, [&](int b) { return C[b].im; }), X[0].ld,
+               tab<const float *>(bt, [&](int b) { return (const float *)V[b].re; }),
+               tab<const float *>(bt, [&](int b) { return (const float *)V[b].im; }), h);
     return APF_OK;
 }
 
-// E ~= Khat^-1 Rin with the stored G_j (block forward sweep + back
-// substitution).  mcols: columns that the forward sweep must carry.
+int inv32(apf_ctx *c, const PV &X, int n, float *Tre, float *Tim, float *Vre, float *Vim, cudaStream_t s) {
+    return inv32_b(one(c), &X, n, &Tre, &Tim, &Vre, &Vim, s);
+}
+
 // Packed operand view of G_j (slot j, or j's slot in its segment).
 PackView gp_view(const apf_ctx *c, int j) {
     const MixedWork *w = c->mw;
@@ -738,44 +949,70 @@ PackView gp_view(const apf_ctx *c, int j) {
     return PackView{w->GP + slot * w->gp_stride, rows, kp, w->nsplit_elim, rows * kp};
 }
 
-// E ~= Khat^-1 Rin with the stored (or recomputed) G_j (block forward sweep +
-// back substitution).  mcols: columns that the forward sweep must carry.
-int approx_solve(apf_ctx *c, const double2 *Rin, double2 *Eout, int mcols, cudaStream_t s) {
+// E[b] ~= Khat[b]^-1 Rin[b] with the stored (or recomputed) G_j of each design
+// (block forward sweep + back substitution).  mcols: columns that the forward
+// sweep must carry.
+int approx_solve_b(const Bat &bt, const double2 *const *Rin, double2 *const *Eout, int mcols, cudaStream_t s) {
+    apf_ctx *c = bt.lead();
     MixedWork *w = c->mw;
-    int ncol = c->cf + c->ca;
-    int nx = c->nx, ns = w->nsplit_elim;
-    long long L = (long long)ncol * nx;
-    float *Ore = w->O32, *Oim = w->O32 + L;
+    const int nb = bt.n;
+    const int ncol = c->cf + c->ca;
+    const int nx = c->nx, ns = w->nsplit_elim;
+    const long long L = (long long)ncol * nx;
     const int K = w->seg_rows;
     // with recomputation: the segment whose inverses row j needs must be loaded
     auto need = [&](int j) -> int {
         if (K <= 0) return APF_OK;
         const int sg = j / K;
         if (sg == w->seg_loaded) return APF_OK;
-        return recompute_segment(c, sg, s);
+        return recompute_segment_b(bt, sg, s);
     };
-    dim3 cgrid((nx + 255) / 256, ncol);
-    cudaMemcpyAsync(Eout, Rin, sizeof(double2) * L, cudaMemcpyDeviceToDevice, s);
+    PV O[TC_MAX_BATCH];
+    __nv_bfloat16 *padst[TC_MAX_BATCH];
+    for (int b = 0; b < nb; ++b) {
+        MixedWork *wb = bt.c[b]->mw;
+        O[b] = PV{wb->O32, wb->O32 + L, nx};
+        padst[b] = wb->PA;
+        cudaMemcpyAsync(Eout[b], Rin[b], sizeof(double2) * L, cudaMemcpyDeviceToDevice, s);
+    }
+    auto otab_re = tab<const float *>(bt, [&](int b) { return (const float *)O[b].re; });
+    auto otab_im = tab<const float *>(bt, [&](int b) { return (const float *)O[b].im; });
+    dim3 cgrid((nx + 255) / 256, ncol, nb);
+    PackView pa[TC_MAX_BATCH], gv[TC_MAX_BATCH];
+    const double2 *src[TC_MAX_BATCH], *src2[TC_MAX_BATCH];
     int rc;
     for (int j = 1; j < c->h; ++j) {
         if (mcols > 0) {
             if ((rc = need(j - 1))) return rc;
-            PackView pa = pack64A(c, w->PA, Eout + (j - 1) * L, nullptr, nx, mcols, nx, ns, s);
-            if ((rc = tc_gemm(c, pa, gp_view(c, j - 1), ns, mcols, 2 * nx, nx, 1.f, 0.f, Ore, Oim, nx, nullptr,
-                              nullptr, 0, s)))
-                return rc;
+            for (int b = 0; b < nb; ++b) {
+                src[b] = Eout[b] + (j - 1) * L;
+                gv[b] = gp_view(bt.c[b], j - 1);
+            }
+            pack64A_b(bt, pa, padst, src, nullptr, nx, mcols, nx, ns, s);
+            if ((rc = gemm_b(bt, pa, gv, ns, mcols, 2 * nx, nx, 1.f, 0.f, O, nullptr, s))) return rc;
         }
-        APF_LAUNCH(c, k_combine, cgrid, 256, 0, s, Eout + j * L, Rin + j * L, Ore, Oim, ncol, mcols, nx);
+        APF_LAUNCH(c, k_combine, cgrid, 256, 0, s, tab<double2 *>(bt, [&](int b) { return Eout[b] + j * L; }),
+                   tab<const double2 *>(bt, [&](int b) { return Rin[b] + j * L; }), otab_re, otab_im, ncol, mcols,
+                   nx);
     }
     for (int j = c->h - 1; j >= 0; --j) {
         if ((rc = need(j))) return rc;
-        const double2 *s2 = (j == c->h - 1) ? nullptr : Eout + (j + 1) * L;
-        PackView pa = pack64A(c, w->PA, Eout + j * L, s2, nx, ncol, nx, ns, s);
-        if ((rc = tc_gemm(c, pa, gp_view(c, j), ns, ncol, 2 * nx, nx, 1.f, 0.f, Ore, Oim, nx, nullptr, nullptr, 0, s)))
-            return rc;
-        APF_LAUNCH(c, k_combine, cgrid, 256, 0, s, Eout + j * L, (const double2 *)nullptr, Ore, Oim, ncol, ncol, nx);
+        for (int b = 0; b < nb; ++b) {
+            src[b] = Eout[b] + j * L;
+            src2[b] = (j == c->h - 1) ? nullptr : Eout[b] + (j + 1) * L;
+            gv[b] = gp_view(bt.c[b], j);
+        }
+        pack64A_b(bt, pa, padst, src, (j == c->h - 1) ? nullptr : src2, nx, ncol, nx, ns, s);
+        if ((rc = gemm_b(bt, pa, gv, ns, ncol, 2 * nx, nx, 1.f, 0.f, O, nullptr, s))) return rc;
+        APF_LAUNCH(c, k_combine, cgrid, 256, 0, s, tab<double2 *>(bt, [&](int b) { return Eout[b] + j * L; }),
+                   tab<const double2 *>(bt, [&](int b) { return (const double2 *)nullptr; }), otab_re, otab_im,
+                   ncol, ncol, nx);
     }
     return APF_OK;
+}
+
+int approx_solve(apf_ctx *c, const double2 *Rin, double2 *Eout, int mcols, cudaStream_t s) {
+    return approx_solve_b(one(c), &Rin, &Eout, mcols, s);
 }
 
 int residual(apf_ctx *c, const double2 *E, double2 *r, cudaStream_t s) {
@@ -818,6 +1055,7 @@ int mixed_alloc(apf_ctx *c) {
     mixed_free(c);
     MixedWork *w = new MixedWork();
     c->mw = w;
+    w->nsplit_elim = c->elim_planes;
     if (const char *e = getenv("APF_NSPLIT_ELIM")) {  // tuning knob: bf16 planes of the elimination (2 or 3)
         int v = atoi(e);
         if (v == 2 || v == 3) w->nsplit_elim = v;
@@ -841,6 +1079,26 @@ int mixed_alloc(apf_ctx *c) {
     w->pb_elems = std::max(n * n * w->nsplit_elim, 2 * n * kp_g * ns_max);
     WA(w->PA, w->pa_elems);
     WA(w->PB, w->pb_elems);
+    if (const char *e = getenv("APF_BUTTERFLY")) w->bfly = (e[0] == '1');  // diagnostic knob; default from ctx
+    else w->bfly = c->butterfly;
+    WA(w->BW, 2 * n);
+    {
+        // random diagonals exp(rho / 10), rho uniform in [-1/2, 1/2) (splitmix64, fixed seed)
+        std::vector<float> bw(2 * n);
+        uint64_t z = 0x9E3779B97F4A7C15ull ^ (uint64_t)n;
+        for (long long i = 0; i < 2 * n; ++i) {
+            z += 0x9E3779B97F4A7C15ull;
+            uint64_t x = z;
+            x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+            x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+            x ^= x >> 31;
+            const double rho = (double)(x >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+            bw[i] = (float)exp(rho / 10.0);
+        }
+        cudaError_t e = cudaMemcpyAsync(w->BW, bw.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice, c->cap_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap_stream);
+        if (e != cudaSuccess) return check_cuda(c, e, "butterfly weights");
+    }
     w->gp_stride = 2 * n * 2 * n * w->nsplit_elim;
     w->seg_rows = (c->schur_seg > 0 && c->schur_seg < h) ? c->schur_seg : 0;
     w->nseg = w->seg_rows > 0 ? (int)((h + w->seg_rows - 1) / w->seg_rows) : 1;
@@ -862,71 +1120,137 @@ int mixed_alloc(apf_ctx *c) {
     return APF_OK;
 }
 
-int mixed_eliminate(apf_ctx *c, cudaStream_t s) {
+// G_j = X_j^-1 in place (the block in w->Xre / w->Xim of every design),
+// through the symmetric random butterfly transform when it is on and the
+// recursion has levels.
+int invert_block_b(const Bat &bt, cudaStream_t s) {
+    apf_ctx *c = bt.lead();
     MixedWork *w = c->mw;
-    if (!w) return set_err(c, APF_ESTATE, "mixed workspace missing");
-    GridDev g = make_grid(c);
-    int n = c->nx;
-    const long long nn = (long long)n * n;
-    const int K = w->seg_rows;
-    dim3 agrid((n / 4 + 255) / 256, n);
-    PV X{w->Xre, w->Xim, n};
-    APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, 0, c->d_eps, c->d_circ, (const float *)nullptr,
-               (const float *)nullptr, w->Xre, w->Xim);
-    for (int j = 0; j < c->h; ++j) {
-        int rc = inv32(c, X, n, w->Tre, w->Tim, w->Vre, w->Vim, s);
-        if (rc) return rc;
-        pack32(c, (__nv_bfloat16 *)gp_view(c, j).base, X, n, n, false, true, w->nsplit_elim, s);
-        if (K > 0 && j + 1 < c->h && (j + 1) % K == 0) {
-            // checkpoint G_j (float32) for the segment that starts at row j + 1
-            float *ck = w->CK + (long long)((j + 1) / K - 1) * 2 * nn;
-            cudaMemcpyAsync(ck, w->Xre, sizeof(float) * nn, cudaMemcpyDeviceToDevice, s);
-            cudaMemcpyAsync(ck + nn, w->Xim, sizeof(float) * nn, cudaMemcpyDeviceToDevice, s);
-        }
-        if (j + 1 < c->h)
-            APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, j + 1, c->d_eps, c->d_circ, w->Xre, w->Xim, w->Xre,
-                       w->Xim);
+    const int n = c->nx, nb = bt.n;
+    PV X[TC_MAX_BATCH];
+    float *tre[TC_MAX_BATCH], *tim[TC_MAX_BATCH], *vre[TC_MAX_BATCH], *vim[TC_MAX_BATCH];
+    for (int b = 0; b < nb; ++b) {
+        MixedWork *wb = bt.c[b]->mw;
+        X[b] = PV{wb->Xre, wb->Xim, n};
+        tre[b] = wb->Tre; tim[b] = wb->Tim; vre[b] = wb->Vre; vim[b] = wb->Vim;
     }
-    w->seg_loaded = K > 0 ? (c->h - 1) / K : -1;
+    const bool bf = w->bfly && n > leaf_size(w) && n >= 16;
+    const dim3 bgrid((n / 4 + 127) / 128, n / 4, nb);
+    auto xre = tab<float *>(bt, [&](int b) { return X[b].re; });
+    auto xim = tab<float *>(bt, [&](int b) { return X[b].im; });
+    if (bf) APF_LAUNCH(c, k_butterfly<false>, bgrid, 128, 0, s, xre, xim, (long long)n, n, (const float *)w->BW);
+    int rc = inv32_b(bt, X, n, tre, tim, vre, vim, s);
+    if (rc) return rc;
+    if (bf) APF_LAUNCH(c, k_butterfly<true>, bgrid, 128, 0, s, xre, xim, (long long)n, n, (const float *)w->BW);
     return APF_OK;
 }
 
-// Recompute the packed inverses of segment `seg` (rows c .. c + seg_rows - 1)
-// into the GP slots: X_c = K_c - G_{c-1} from the float32 checkpoint, then the
-// same inversions and assemblies as the elimination (bit-identical results).
-int recompute_segment(apf_ctx *c, int seg, cudaStream_t s) {
+// X_row = K_row - G (G: the float32 planes gre/gim of each design, or none) into w->Xre / w->Xim.
+static void assemble_b(const Bat &bt, int row, const float *const *gre, const float *const *gim, cudaStream_t s) {
+    apf_ctx *c = bt.lead();
+    const int n = c->nx;
+    dim3 agrid((n / 4 + 255) / 256, n, bt.n);
+    APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, make_grid(c), row,
+               tab<const double *>(bt, [&](int b) { return (const double *)bt.c[b]->d_eps; }),
+               (const double2 *)c->d_circ, tab<const float *>(bt, [&](int b) { return gre ? gre[b] : nullptr; }),
+               tab<const float *>(bt, [&](int b) { return gim ? gim[b] : nullptr; }),
+               tab<float *>(bt, [&](int b) { return bt.c[b]->mw->Xre; }),
+               tab<float *>(bt, [&](int b) { return bt.c[b]->mw->Xim; }));
+}
+
+// Pack every design's G_j (its working block) into its GP slot of row j.
+static void pack_gp_b(const Bat &bt, int j, cudaStream_t s) {
+    const int n = bt.lead()->nx;
+    PackView v[TC_MAX_BATCH];
+    PV X[TC_MAX_BATCH];
+    __nv_bfloat16 *dst[TC_MAX_BATCH];
+    for (int b = 0; b < bt.n; ++b) {
+        MixedWork *wb = bt.c[b]->mw;
+        X[b] = PV{wb->Xre, wb->Xim, n};
+        dst[b] = (__nv_bfloat16 *)gp_view(bt.c[b], j).base;
+    }
+    pack32_b(bt, v, dst, X, n, n, false, true, bt.lead()->mw->nsplit_elim, s);
+}
+
+int mixed_eliminate_b(const Bat &bt, cudaStream_t s) {
+    apf_ctx *c = bt.lead();
+    for (int b = 0; b < bt.n; ++b)
+        if (!bt.c[b]->mw) return set_err(bt.c[b], APF_ESTATE, "mixed workspace missing");
     MixedWork *w = c->mw;
-    GridDev g = make_grid(c);
+    const int n = c->nx;
+    const long long nn = (long long)n * n;
+    const int K = w->seg_rows;
+    const float *xre[TC_MAX_BATCH], *xim[TC_MAX_BATCH];
+    for (int b = 0; b < bt.n; ++b) { xre[b] = bt.c[b]->mw->Xre; xim[b] = bt.c[b]->mw->Xim; }
+    assemble_b(bt, 0, nullptr, nullptr, s);
+    for (int j = 0; j < c->h; ++j) {
+        int rc = invert_block_b(bt, s);
+        if (rc) return rc;
+        pack_gp_b(bt, j, s);
+        if (K > 0 && j + 1 < c->h && (j + 1) % K == 0) {
+            // checkpoint G_j (float32) for the segment that starts at row j + 1
+            for (int b = 0; b < bt.n; ++b) {
+                MixedWork *wb = bt.c[b]->mw;
+                float *ck = wb->CK + (long long)((j + 1) / K - 1) * 2 * nn;
+                cudaMemcpyAsync(ck, wb->Xre, sizeof(float) * nn, cudaMemcpyDeviceToDevice, s);
+                cudaMemcpyAsync(ck + nn, wb->Xim, sizeof(float) * nn, cudaMemcpyDeviceToDevice, s);
+            }
+        }
+        if (j + 1 < c->h) assemble_b(bt, j + 1, xre, xim, s);
+    }
+    for (int b = 0; b < bt.n; ++b) bt.c[b]->mw->seg_loaded = K > 0 ? (c->h - 1) / K : -1;
+    return APF_OK;
+}
+
+int mixed_eliminate(apf_ctx *c, cudaStream_t s) { return mixed_eliminate_b(one(c), s); }
+
+// Recompute the packed inverses of segment `seg` (rows c .. c + seg_rows - 1)
+// into the GP slots of every design: X_c = K_c - G_{c-1} from the float32
+// checkpoint, then the same inversions and assemblies as the elimination
+// (bit-identical results).
+int recompute_segment_b(const Bat &bt, int seg, cudaStream_t s) {
+    apf_ctx *c = bt.lead();
+    MixedWork *w = c->mw;
     const int n = c->nx, K = w->seg_rows;
     const long long nn = (long long)n * n;
     const int r0 = seg * K, r1 = std::min(c->h, r0 + K);
-    dim3 agrid((n / 4 + 255) / 256, n);
-    PV X{w->Xre, w->Xim, n};
-    const float *gre = seg > 0 ? w->CK + (long long)(seg - 1) * 2 * nn : nullptr;
-    const float *gim = seg > 0 ? gre + nn : nullptr;
-    APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, r0, c->d_eps, c->d_circ, gre, gim, w->Xre, w->Xim);
-    for (int j = r0; j < r1; ++j) {
-        int rc = inv32(c, X, n, w->Tre, w->Tim, w->Vre, w->Vim, s);
-        if (rc) return rc;
-        pack32(c, (__nv_bfloat16 *)gp_view(c, j).base, X, n, n, false, true, w->nsplit_elim, s);
-        if (j + 1 < r1)
-            APF_LAUNCH(c, k_assemble32, agrid, 256, 0, s, g, j + 1, c->d_eps, c->d_circ, w->Xre, w->Xim, w->Xre,
-                       w->Xim);
+    const float *gre[TC_MAX_BATCH], *gim[TC_MAX_BATCH], *xre[TC_MAX_BATCH], *xim[TC_MAX_BATCH];
+    for (int b = 0; b < bt.n; ++b) {
+        MixedWork *wb = bt.c[b]->mw;
+        gre[b] = seg > 0 ? wb->CK + (long long)(seg - 1) * 2 * nn : nullptr;
+        gim[b] = seg > 0 ? gre[b] + nn : nullptr;
+        xre[b] = wb->Xre;
+        xim[b] = wb->Xim;
     }
-    w->seg_loaded = seg;
+    assemble_b(bt, r0, seg > 0 ? gre : nullptr, seg > 0 ? gim : nullptr, s);
+    for (int j = r0; j < r1; ++j) {
+        int rc = invert_block_b(bt, s);
+        if (rc) return rc;
+        pack_gp_b(bt, j, s);
+        if (j + 1 < r1) assemble_b(bt, j + 1, xre, xim, s);
+    }
+    for (int b = 0; b < bt.n; ++b) bt.c[b]->mw->seg_loaded = seg;
     return APF_OK;
 }
 
 // Right-hand side R (written into d_E by the caller), its column norms, and
 // the first low-precision solve E = Khat^-1 R.
-int mixed_fields_begin(apf_ctx *c, cudaStream_t s) {
-    MixedWork *w = c->mw;
-    int ncol = c->cf + c->ca;
-    long long total = (long long)ncol * c->nx * c->h;
-    cudaMemcpyAsync(c->d_R, c->d_Ew, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s);
-    APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, c->d_R, c->h, ncol, c->nx, w->rnorm);
-    return approx_solve(c, c->d_R, c->d_Ew, c->cf, s);
+int mixed_fields_begin_b(const Bat &bt, cudaStream_t s) {
+    const double2 *R[TC_MAX_BATCH];
+    double2 *E[TC_MAX_BATCH];
+    for (int b = 0; b < bt.n; ++b) {
+        apf_ctx *c = bt.c[b];
+        const int ncol = c->cf + c->ca;
+        const long long total = (long long)ncol * c->nx * c->h;
+        cudaMemcpyAsync(c->d_R, c->d_Ew, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s);
+        APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, c->d_R, c->h, ncol, c->nx, c->mw->rnorm);
+        R[b] = c->d_R;
+        E[b] = c->d_Ew;
+    }
+    return approx_solve_b(bt, R, E, bt.lead()->cf, s);
 }
+
+int mixed_fields_begin(apf_ctx *c, cudaStream_t s) { return mixed_fields_begin_b(one(c), s); }
 
 static int resid_body(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
@@ -936,15 +1260,26 @@ static int resid_body(apf_ctx *c, cudaStream_t s) {
     return APF_OK;
 }
 
-static int correct_body(apf_ctx *c, cudaStream_t s) {
-    MixedWork *w = c->mw;
-    int ncol = c->cf + c->ca;
-    long long total = (long long)ncol * c->nx * c->h;
-    int rc = approx_solve(c, w->r, w->delta, ncol, s);
+// E += Khat^-1 r for every design of the batch.
+static int correct_b(const Bat &bt, cudaStream_t s) {
+    const double2 *r[TC_MAX_BATCH];
+    double2 *d[TC_MAX_BATCH];
+    for (int b = 0; b < bt.n; ++b) {
+        r[b] = bt.c[b]->mw->r;
+        d[b] = bt.c[b]->mw->delta;
+    }
+    apf_ctx *c0 = bt.lead();
+    int rc = approx_solve_b(bt, r, d, c0->cf + c0->ca, s);
     if (rc) return rc;
-    APF_LAUNCH(c, k_axpy, (unsigned)((total + 255) / 256), 256, 0, s, c->d_Ew, w->delta, total);
+    for (int b = 0; b < bt.n; ++b) {
+        apf_ctx *c = bt.c[b];
+        const long long total = (long long)(c->cf + c->ca) * c->nx * c->h;
+        APF_LAUNCH(c, k_axpy, (unsigned)((total + 255) / 256), 256, 0, s, c->d_Ew, c->mw->delta, total);
+    }
     return APF_OK;
 }
+
+static int correct_body(apf_ctx *c, cudaStream_t s) { return correct_b(one(c), s); }
 
 // Diagnostics: APF_IR_VERBOSE=1 prints the residual of every refinement step.
 static const bool g_ir_verbose = [] {
@@ -1122,21 +1457,121 @@ int mixed_refine(apf_ctx *c, cudaStream_t s) {
 
 // Gradient contraction with tensor-core products: Q_j = Gamma F_j, then
 // g_j(x) = 2 k^2 Re sum_b Phi_j[b][x] Q_j[b][x] in float64.
-int mixed_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s) {
+// Gradient contraction with tensor-core products for every design of the
+// batch: Q_j = Gamma F_j, then g_j(x) = 2 k^2 Re sum_b Phi_j[b][x] Q_j[b][x] in
+// float64.  Gamma[b]: the design's n_out x n_in Gamma on the device.
+int mixed_gradient_b(const Bat &bt, const double2 *const *Gamma, cudaStream_t s) {
+    apf_ctx *c = bt.lead();
     MixedWork *w = c->mw;
-    int nin = c->nin, nout = c->nout, ncol = nin + nout;
-    int nx = c->nx, ns = w->nsplit_grad;
-    long long L = (long long)ncol * nx;
-    PackView pa = pack64A(c, w->PA, Gamma, nullptr, nin, nout, nin, ns, s);
-    float *Qre = w->O32, *Qim = w->O32 + (long long)nout * nx;
+    const int nin = c->nin, nout = c->nout, ncol = nin + nout;
+    const int nx = c->nx, ns = w->nsplit_grad, nb = bt.n;
+    const long long L = (long long)ncol * nx;
+    PackView pa[TC_MAX_BATCH], pb[TC_MAX_BATCH];
+    __nv_bfloat16 *padst[TC_MAX_BATCH], *pbdst[TC_MAX_BATCH];
+    PV Q[TC_MAX_BATCH];
+    const double2 *src[TC_MAX_BATCH];
+    for (int b = 0; b < nb; ++b) {
+        MixedWork *wb = bt.c[b]->mw;
+        padst[b] = wb->PA;
+        pbdst[b] = wb->PB;
+        Q[b] = PV{wb->O32, wb->O32 + (long long)nout * nx, nx};
+    }
+    pack64A_b(bt, pa, padst, Gamma, nullptr, nin, nout, nin, ns, s);
     for (int j = 0; j < c->h; ++j) {
-        PackView pb = pack64BT(c, w->PB, c->d_E + j * L, nx, nx, nin, ns, s);
-        int rc = tc_gemm(c, pa, pb, ns, nout, 2 * nx, nx, 1.f, 0.f, Qre, Qim, nx, nullptr, nullptr, 0, s);
+        for (int b = 0; b < nb; ++b) src[b] = bt.c[b]->d_E + j * L;
+        pack64BT_b(bt, pb, pbdst, src, nx, nx, nin, ns, s);
+        int rc = gemm_b(bt, pa, pb, ns, nout, 2 * nx, nx, 1.f, 0.f, Q, nullptr, s);
         if (rc) return rc;
-        APF_LAUNCH(c, k_grad_rowdot32, (nx + 31) / 32, 256, 0, s, c->d_E, Qre, Qim, j, nx, nin, nout, c->k * c->k,
-                   c->d_grad);
+        APF_LAUNCH(c, k_grad_rowdot32, dim3((nx + 31) / 32, 1, nb), 256, 0, s,
+                   tab<const double2 *>(bt, [&](int b) { return (const double2 *)bt.c[b]->d_E; }),
+                   tab<const float *>(bt, [&](int b) { return (const float *)Q[b].re; }),
+                   tab<const float *>(bt, [&](int b) { return (const float *)Q[b].im; }), j, nx, nin, nout,
+                   c->k * c->k, tab<double *>(bt, [&](int b) { return bt.c[b]->d_grad; }));
     }
     return APF_OK;
+}
+
+int mixed_gradient(apf_ctx *c, const double2 *Gamma, cudaStream_t s) { return mixed_gradient_b(one(c), &Gamma, s); }
+
+// Refinement of a batch of designs (no captured graphs): every sweep checks
+// the residual of each design, and designs still above tolerance take one
+// more correction, all of them in the same launches.  The stopping rule per
+// design is that of mixed_refine.  rc[b]: APF_OK or APF_ENOCONV.
+int mixed_refine_b(const Bat &bt, cudaStream_t s, int *rcs) {
+    const int nb = bt.n;
+    apf_ctx *c0 = bt.lead();
+    const int ncol = c0->cf + c0->ca;
+    std::vector<std::vector<double>> nr(nb, std::vector<double>(ncol)), ne(nb, std::vector<double>(ncol));
+    std::vector<int> iters(nb, 0), rising(nb, 0), active(nb, 1);
+    std::vector<double> ratio(nb, 0.0), prev(nb, INFINITY);
+    for (;;) {
+        for (int b = 0; b < nb; ++b) {
+            if (!active[b]) continue;
+            apf_ctx *c = bt.c[b];
+            resid_body(c, s);
+            cudaMemcpyAsync(nr[b].data(), c->mw->rnorm, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(ne[b].data(), c->mw->rnorm + ncol, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
+        }
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return check_cuda(c0, e, "refinement");
+        Bat next;
+        next.n = 0;
+        for (int b = 0; b < nb; ++b) {
+            if (!active[b]) continue;
+            apf_ctx *c = bt.c[b];
+            double r = 0.0;
+            for (int i = 0; i < ncol; ++i) r = std::max(r, sqrt(ne[b][i] / std::max(nr[b][i], 1e-300)));
+            ratio[b] = (r == r) ? r : INFINITY;
+            bool stop = !(r == r) || r <= c->ir_tol || iters[b] >= c->ir_max;
+            if (!stop) {
+                rising[b] = r > prev[b] ? rising[b] + 1 : 0;
+                stop = rising[b] >= 2;
+            }
+            prev[b] = r;
+            if (stop) active[b] = 0;
+            else next.c[next.n++] = c;
+        }
+        if (next.n == 0) break;
+        int rc = correct_b(next, s);
+        if (rc) return rc;
+        for (int b = 0; b < nb; ++b)
+            if (active[b]) ++iters[b];
+    }
+    for (int b = 0; b < nb; ++b) {
+        apf_ctx *c = bt.c[b];
+        c->stats.refine_iters = iters[b];
+        c->stats.residual = ratio[b];
+        rcs[b] = ratio[b] <= c->ir_tol ? APF_OK : APF_ENOCONV;
+    }
+    return APF_OK;
+}
+
+// Entry points for a batch of contexts (apf_solve_S_grad_batch).
+static Bat make_bat(apf_ctx *const *cs, int nb) {
+    Bat bt;
+    bt.n = nb;
+    for (int b = 0; b < nb; ++b) bt.c[b] = cs[b];
+    return bt;
+}
+int mixed_eliminate_n(apf_ctx *const *cs, int nb, cudaStream_t s) { return mixed_eliminate_b(make_bat(cs, nb), s); }
+int mixed_fields_begin_n(apf_ctx *const *cs, int nb, cudaStream_t s) {
+    return mixed_fields_begin_b(make_bat(cs, nb), s);
+}
+int mixed_refine_n(apf_ctx *const *cs, int nb, cudaStream_t s, int *rcs) {
+    return mixed_refine_b(make_bat(cs, nb), s, rcs);
+}
+int mixed_gradient_n(apf_ctx *const *cs, int nb, cudaStream_t s) {
+    const double2 *g[TC_MAX_BATCH];
+    for (int b = 0; b < nb; ++b) g[b] = cs[b]->d_Gam;
+    return mixed_gradient_b(make_bat(cs, nb), g, s);
+}
+// Settings that must agree across the designs of a batch (the launches are shared).
+bool mixed_batch_compatible(const apf_ctx *a, const apf_ctx *b) {
+    const MixedWork *x = a->mw, *y = b->mw;
+    if (!x || !y) return false;
+    return x->nsplit_elim == y->nsplit_elim && x->nsplit_grad == y->nsplit_grad && x->leaf == y->leaf &&
+           x->leaf_variant == y->leaf_variant && x->seg_rows == y->seg_rows && x->bfly == y->bfly && x->km == 0 &&
+           y->km == 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1178,10 +1613,20 @@ extern "C" int apf_debug_inv32(apf_ctx *c, int n, float *re, float *im, int leaf
     if (!c || !c->mw || n < 1 || n > c->nx || (n & (n - 1))) return APF_EINVAL;
     cudaSetDevice(c->device);
     int old = c->mw->leaf, oldv = c->mw->leaf_variant;
-    // leaf = block size + 1000 * kernel variant (test and tuning hook)
+    // leaf = block size + 1000 * kernel variant (test and tuning hook);
+    // + 100000: through the symmetric random butterfly transform
+    const bool bf = leaf >= 100000 && n >= 16;
+    leaf %= 100000;
     if (leaf > 0) { c->mw->leaf = leaf % 1000; c->mw->leaf_variant = leaf / 1000; }
     cudaMemset(c->d_flags, 0, 16);
+    const dim3 bgrid((n / 4 + 127) / 128, n / 4);
+    Tab<float *> tre{}, tim{};
+    tre.v[0] = re;
+    tim.v[0] = im;
+    if (bf) APF_LAUNCH(c, k_butterfly<false>, bgrid, 128, 0, (cudaStream_t)0, tre, tim, (long long)n, n, (const float *)c->mw->BW);
     int rc = inv32(c, PV{re, im, n}, n, c->mw->Tre, c->mw->Tim, c->mw->Vre, c->mw->Vim, 0);
+    if (bf && rc == APF_OK)
+        APF_LAUNCH(c, k_butterfly<true>, bgrid, 128, 0, (cudaStream_t)0, tre, tim, (long long)n, n, (const float *)c->mw->BW);
     cudaError_t e = cudaDeviceSynchronize();
     c->mw->leaf = old;
     c->mw->leaf_variant = oldv;

@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <stdlib.h>
+#include <string.h>
 
 namespace {
 
@@ -179,10 +180,10 @@ __device__ __forceinline__ void store_chunk(const TcParams &p, int row, int col0
 // Persistent: one CTA per SM walks the output tiles (M index fastest, so the
 // CTAs working on one B panel run together); two tensor-memory accumulators
 // let the epilogue of one tile overlap the MMAs of the next.
-template <int BN, int STAGES>
-__global__ void __launch_bounds__(192, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+template <int BN, int STAGES, int P>
+__global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcArgs<P> args) {
     using L = Layout<BN, STAGES>;
+    const TcParams &p = args.p[0];  // shape and precision: the same for every problem
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + L::BAR);
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(192, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int Mt = (p.M + BM - 1) / BM, Nt = (p.N + BN - 1) / BN;
-    const int ntiles = Mt * Nt;
+    const int ntl = Mt * Nt, ntiles = ntl * args.nprob;  // tiles of problem pr: [pr ntl, (pr + 1) ntl)
     const int total = p.nseg * p.kblocks;
 
     if (threadIdx.x == 0) {
@@ -227,7 +228,9 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             int it = 0;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                const int m0 = (tile % Mt) * BM, n0 = (tile / Mt) * BN;
+                const int pr = tile / ntl, tt = tile - pr * ntl;
+                const int m0 = (tt % Mt) * BM, n0 = (tt / Mt) * BN;
+                const CUtensorMap *tmA = &args.a[pr], *tmB = &args.b[pr];
                 for (int kk = 0; kk < total; ++kk, ++it) {
                     const int s = it % STAGES, r = it / STAGES;
                     if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) { ok = false; break; }
@@ -236,8 +239,8 @@ __global__ void __launch_bounds__(192, 1)
                     uint8_t *sa = smem + s * L::STAGE;
                     uint8_t *sb = sa + L::A_BYTES;
                     mbar_expect_tx(&full[s], L::A_BYTES + L::B_BYTES);
-                    tma_load_3d(sa, &tmA, &full[s], kb * BK, m0, pa);
-                    tma_load_3d(sb, &tmB, &full[s], kb * BK, n0, pb);
+                    tma_load_3d(sa, tmA, &full[s], kb * BK, m0, pa);
+                    tma_load_3d(sb, tmB, &full[s], kb * BK, n0, pb);
                     issued = it + 1;
                 }
             }
@@ -280,13 +283,14 @@ __global__ void __launch_bounds__(192, 1)
             const int b = tl & 1, u = tl >> 1;
             if (!mbar_wait(&tfull[b], u & 1, abort_flag)) { ok = false; break; }
             fence_after();
-            const int m0 = (tile % Mt) * BM, n0 = (tile / Mt) * BN;
+            const int pr = tile / ntl, tt = tile - pr * ntl;
+            const int m0 = (tt % Mt) * BM, n0 = (tt / Mt) * BN;
             const int row = m0 + 32 * q + lane;
 #pragma unroll 1
             for (int c = 0; c < BN; c += 32) {
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + c), r);
-                store_chunk(p, row, n0 + c, r);
+                store_chunk(args.p[pr], row, n0 + c, r);
             }
             fence_before();
             __syncwarp();
@@ -295,7 +299,8 @@ __global__ void __launch_bounds__(192, 1)
     }
     if (!ok) {
         *abort_flag = 1;
-        if (p.flags) atomicOr(p.flags, FLAG_TIMEOUT);
+        for (int pr = 0; pr < args.nprob; ++pr)
+            if (args.p[pr].flags) atomicOr(args.p[pr].flags, FLAG_TIMEOUT);
     }
     __syncwarp();
     // after a failure anywhere, wait (bounded) for the producer's copies in flight
@@ -389,10 +394,10 @@ struct PairLayout {
 
 constexpr int PAIR_TMEM_COLS = 512;
 
-template <int BN, int STAGES>
-__global__ void __launch_bounds__(192, 1)
-    k_tc_gemm_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+template <int BN, int STAGES, int P>
+__global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__ TcArgs<P> args) {
     using L = PairLayout<BN, STAGES>;
+    const TcParams &p = args.p[0];  // shape: the same for every problem
     constexpr int BNH = L::BNH;
     extern __shared__ uint8_t smem_raw[];
     // same offset in both CTAs: the MMA addresses both CTAs' tiles with one descriptor
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t rank = cluster_rank();
     const bool lead = (rank == 0);
     const int Mt2 = (p.M + 2 * BM - 1) / (2 * BM), Nt = (p.N + BN - 1) / BN;
-    const int ntiles = Mt2 * Nt;
+    const int ntl = Mt2 * Nt, ntiles = ntl * args.nprob;  // tiles of problem pr: [pr ntl, (pr + 1) ntl)
     const int cid = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
     const int total = p.kblocks;
 
@@ -442,7 +447,9 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             int it = 0;
             for (int t = cid; t < ntiles && ok; t += ncl) {
-                const int m0 = (t % Mt2) * 2 * BM + (int)rank * BM, n0 = (t / Mt2) * BN + (int)rank * BNH;
+                const int pr = t / ntl, tt = t - pr * ntl;
+                const int m0 = (tt % Mt2) * 2 * BM + (int)rank * BM, n0 = (tt / Mt2) * BN + (int)rank * BNH;
+                const CUtensorMap *tmA = &args.a[pr], *tmB = &args.b[pr];
                 for (int kk = 0; kk < total; ++kk, ++it) {
                     const int s = it % STAGES, r = it / STAGES;
                     if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag)) { ok = false; break; }
@@ -451,10 +458,10 @@ __global__ void __launch_bounds__(192, 1)
                     uint8_t *sa = smem + s * L::STAGE;
                     uint8_t *sb = sa + 2 * L::A_PLANE;
                     // [A plane 0 | A plane 1 | B plane 0 | B plane 1]
-                    tma_load_3d_pair(sa, &tmA, fb, kk * BK, m0, 0);
-                    tma_load_3d_pair(sa + L::A_PLANE, &tmA, fb, kk * BK, m0, 1);
-                    tma_load_3d_pair(sb, &tmB, fb, kk * BK, n0, 0);
-                    tma_load_3d_pair(sb + L::B_PLANE, &tmB, fb, kk * BK, n0, 1);
+                    tma_load_3d_pair(sa, tmA, fb, kk * BK, m0, 0);
+                    tma_load_3d_pair(sa + L::A_PLANE, tmA, fb, kk * BK, m0, 1);
+                    tma_load_3d_pair(sb, tmB, fb, kk * BK, n0, 0);
+                    tma_load_3d_pair(sb + L::B_PLANE, tmB, fb, kk * BK, n0, 1);
                     issued = it + 1;
                 }
             }
@@ -505,13 +512,14 @@ __global__ void __launch_bounds__(192, 1)
             const int b = tl & 1, u = tl >> 1;
             if (!mbar_wait(&tfull[b], u & 1, abort_flag)) { ok = false; break; }
             fence_after();
-            const int m0 = (t % Mt2) * 2 * BM + (int)rank * BM, n0 = (t / Mt2) * BN;
+            const int pr = t / ntl, tt = t - pr * ntl;
+            const int m0 = (tt % Mt2) * 2 * BM + (int)rank * BM, n0 = (tt / Mt2) * BN;
             const int row = m0 + 32 * q + lane;
 #pragma unroll 1
             for (int c = 0; c < BN; c += 32) {
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + c), r);
-                store_chunk(p, row, n0 + c, r);
+                store_chunk(args.p[pr], row, n0 + c, r);
             }
             fence_before();
             __syncwarp();
@@ -520,7 +528,8 @@ __global__ void __launch_bounds__(192, 1)
     }
     if (!ok) {
         *abort_flag = 1;
-        if (p.flags) atomicOr(p.flags, FLAG_TIMEOUT);
+        for (int pr = 0; pr < args.nprob; ++pr)
+            if (args.p[pr].flags) atomicOr(args.p[pr].flags, FLAG_TIMEOUT);
     }
     __syncwarp();
     // after a failure, the even CTA waits (bounded) for the copies in flight of both CTAs
@@ -567,7 +576,9 @@ bool make_map(CUtensorMap *m, const PackView &v, int box_rows) {
 
 template <int BN, int STAGES>
 void set_attr() {
-    cudaFuncSetAttribute(k_tc_gemm<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tc_gemm<BN, STAGES, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         Layout<BN, STAGES>::TOTAL);
+    cudaFuncSetAttribute(k_tc_gemm<BN, STAGES, TC_MAX_BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          Layout<BN, STAGES>::TOTAL);
 }
 
@@ -588,9 +599,13 @@ uint32_t tc_seg_pairs(int nsplit, int *nseg) {
 void tc_init_attrs() {
     set_attr<256, 4>();
     set_attr<128, 6>();
-    cudaFuncSetAttribute(k_tc_gemm_pair<256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tc_gemm_pair<256, 3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          PairLayout<256, 3>::TOTAL);
-    cudaFuncSetAttribute(k_tc_gemm_pair<192, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tc_gemm_pair<192, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         PairLayout<192, 4>::TOTAL);
+    cudaFuncSetAttribute(k_tc_gemm_pair<256, 3, TC_MAX_BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         PairLayout<256, 3>::TOTAL);
+    cudaFuncSetAttribute(k_tc_gemm_pair<192, 4, TC_MAX_BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          PairLayout<192, 4>::TOTAL);
 }
 
@@ -623,7 +638,7 @@ static int max_pair_clusters() {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, k_tc_gemm_pair<256, 3>, &cfg) != cudaSuccess || n <= 0) {
+        if (cudaOccupancyMaxActiveClusters(&n, k_tc_gemm_pair<256, 3, 1>, &cfg) != cudaSuccess || n <= 0) {
             cudaGetLastError();
             n = 1 << 20;  // unknown: bounded by the SM count below
         }
@@ -632,21 +647,80 @@ static int max_pair_clusters() {
     return v;
 }
 
-int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M, int N, int n_cplx, float alpha,
-            float beta, float *out_re, float *out_im, long long ldo, const float *in_re, const float *in_im,
-            long long ldi, cudaStream_t s) {
-    if (M <= 0 || N <= 0) return APF_OK;
+namespace {
+
+template <int P, typename K>
+cudaError_t launch_args(apf_ctx *c, K kern, bool pair, unsigned grid, int smem, cudaStream_t s, const TcArgs<P> &args) {
+    if (!pair) {
+        kern<<<grid, 192, smem, s>>>(args);
+        c->launches++;
+        return cudaSuccess;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args);
+    if (e == cudaSuccess) c->launches++;
+    return e;
+}
+
+// Fill the tensor maps and parameters of nprob problems and launch kernel
+// variant `kind` (0: one-CTA 128-wide, 1: one-CTA 256-wide, 2: pair 256, 3: pair 192).
+template <int P>
+int launch_variant(apf_ctx *c, int kind, int nprob, const TcProblem *pb, const TcParams &base, unsigned grid,
+                   cudaStream_t s) {
+    TcArgs<P> args;
+    memset(&args, 0, sizeof args);
+    args.nprob = nprob;
+    const int brows = kind == 0 ? 128 : kind == 1 ? 256 : kind == 2 ? 128 : 96;
+    for (int i = 0; i < nprob; ++i) {
+        if (!make_map(&args.a[i], pb[i].A, BM) || !make_map(&args.b[i], pb[i].B, brows))
+            return set_err(c, APF_ECUDA, "tensor map encode failed (M=%d N=%d kp=%lld)", base.M, base.N, pb[i].A.kp);
+        TcParams q = base;
+        q.out_re = pb[i].out_re; q.out_im = pb[i].out_im;
+        q.in_re = pb[i].in_re ? pb[i].in_re : pb[i].out_re;
+        q.in_im = pb[i].in_im ? pb[i].in_im : pb[i].out_im;
+        q.flags = pb[i].flags;
+        args.p[i] = q;
+    }
+    cudaError_t e = cudaSuccess;
+    switch (kind) {
+        case 0: e = launch_args(c, k_tc_gemm<128, 6, P>, false, grid, Layout<128, 6>::TOTAL, s, args); break;
+        case 1: e = launch_args(c, k_tc_gemm<256, 4, P>, false, grid, Layout<256, 4>::TOTAL, s, args); break;
+        case 2: e = launch_args(c, k_tc_gemm_pair<256, 3, P>, true, grid, PairLayout<256, 3>::TOTAL, s, args); break;
+        default: e = launch_args(c, k_tc_gemm_pair<192, 4, P>, true, grid, PairLayout<192, 4>::TOTAL, s, args); break;
+    }
+    if (e != cudaSuccess) return check_cuda(c, e, "tensor-core GEMM launch");
+    return APF_OK;
+}
+
+}  // namespace
+
+int tc_gemm_n(apf_ctx *c, int nprob, const TcProblem *pb, int nsplit, int M, int N, int n_cplx, float alpha,
+              float beta, long long ldo, long long ldi, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || nprob <= 0) return APF_OK;
+    if (nprob > TC_MAX_BATCH) return set_err(c, APF_EINVAL, "tc_gemm_n: %d problems > %d", nprob, TC_MAX_BATCH);
     if (!ensure_encode()) return set_err(c, APF_ECUDA, "cuTensorMapEncodeTiled unavailable");
-    if (A.kp != B.kp || A.kp % BK != 0) return set_err(c, APF_EINVAL, "tc_gemm: K mismatch (%lld vs %lld)", A.kp, B.kp);
+    for (int i = 0; i < nprob; ++i)
+        if (pb[i].A.kp != pb[i].B.kp || pb[i].A.kp % BK != 0 || pb[i].A.kp != pb[0].A.kp)
+            return set_err(c, APF_EINVAL, "tc_gemm: K mismatch (%lld vs %lld)", pb[i].A.kp, pb[i].B.kp);
+    const long long kp = pb[0].A.kp;
     TcParams p{};
     p.M = M; p.N = N; p.n_cplx = n_cplx;
-    p.kblocks = (int)(A.kp / BK);
+    p.kblocks = (int)(kp / BK);
     p.seg_pairs = tc_seg_pairs(nsplit, &p.nseg);
     p.alpha = alpha; p.beta = beta;
-    p.out_re = out_re; p.out_im = out_im; p.ldo = ldo;
-    p.in_re = in_re ? in_re : out_re; p.in_im = in_im ? in_im : out_im; p.ldi = in_re ? ldi : ldo;
-    p.flags = c->d_flags;
-    CUtensorMap ma, mb;
+    p.ldo = ldo;
+    p.ldi = pb[0].in_re ? ldi : ldo;
     // Tile width: score the wave utilisation of 256- and 128-wide tiles.
     static int num_sms = 0;
     if (!num_sms) {
@@ -656,7 +730,7 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
         if (num_sms <= 0) num_sms = 148;
     }
     auto util = [&](int bn) {
-        long long t = (long long)((N + bn - 1) / bn) * ((M + BM - 1) / BM);
+        long long t = (long long)nprob * ((N + bn - 1) / bn) * ((M + BM - 1) / BM);
         long long waves = (t + num_sms - 1) / num_sms;
         return (double)t / (double)(waves * num_sms);
     };
@@ -664,9 +738,7 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
     // unless they waste much more of the last wave
     bool wide = (N > 128) && util(256) >= 0.7 * util(128);
     int bn = wide ? 256 : 128;
-    if (!make_map(&ma, A, BM) || !make_map(&mb, B, bn))
-        return set_err(c, APF_ECUDA, "tensor map encode failed (M=%d N=%d kp=%lld)", M, N, A.kp);
-    long long ntiles = (long long)((N + bn - 1) / bn) * ((M + BM - 1) / BM);
+    long long ntiles = (long long)nprob * ((N + bn - 1) / bn) * ((M + BM - 1) / BM);
     // leave a few SMs free so that kernels of other streams (concurrent designs'
     // diagonal-block inversions, which cannot share an SM with a GEMM CTA) progress
     static int reserve = -1;
@@ -676,53 +748,42 @@ int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M,
         if (reserve < 0 || reserve > num_sms / 2) reserve = 4;
         if (num_sms <= 64) reserve = 0;
     }
-    dim3 grid((unsigned)std::min<long long>(ntiles, num_sms - reserve));
-    int pi = -1;
-    if (c->prof_on && 2 * (c->prof_used + 1) <= (int)c->prof_ev.size()) {
-        pi = c->prof_used++;
-        // complex m x k x n product: M = m, N = 2n, kp ~ 2k real
-        double alg = 2.0 * (double)M * (double)N * (double)A.kp;
-        c->prof_alg[pi] = alg;
-        c->prof_hw[pi] = alg * p.nseg;
-        record_event(c, c->prof_ev[2 * pi], s);
-    }
-    constexpr int smem_wide = Layout<256, 4>::TOTAL, smem_narrow = Layout<128, 6>::TOTAL;
+    unsigned grid = (unsigned)std::min<long long>(ntiles, num_sms - reserve);
+    int kind = wide ? 1 : 0;
     const int mt = (M + BM - 1) / BM;
     // Pair tiles (256 x BN over two SMs) for wide two-plane products; the tile
     // width BN in {256, 192} that fills the waves of pair slots best.
     const int pair_slots = std::max(1, std::min(max_pair_clusters(), (num_sms - reserve) / 2));
-    if (pair_enabled() && nsplit == 2 && mt >= 2 && N >= 256 && pair_slots >= 1) {
-        auto pair_util = [&](int bn) {
-            long long t = (long long)((M + 2 * BM - 1) / (2 * BM)) * ((N + bn - 1) / bn);
+    if (pair_enabled() && nsplit == 2 && mt >= 2 && N >= 256) {
+        auto pair_util = [&](int pbn) {
+            long long t = (long long)nprob * ((M + 2 * BM - 1) / (2 * BM)) * ((N + pbn - 1) / pbn);
             long long waves = (t + pair_slots - 1) / pair_slots;
             return (double)t / (double)(waves * pair_slots);
         };
         const int pbn = pair_util(192) > 1.1 * pair_util(256) ? 192 : 256;
-        CUtensorMap mbh;
-        if (!make_map(&mbh, B, pbn / 2)) return set_err(c, APF_ECUDA, "tensor map encode failed (half B)");
-        long long ntp = (long long)((M + 2 * BM - 1) / (2 * BM)) * ((N + pbn - 1) / pbn);
-        long long ncl = std::min<long long>(ntp, pair_slots);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(2 * ncl));
-        cfg.blockDim = dim3(192);
-        cfg.dynamicSmemBytes = pbn == 256 ? PairLayout<256, 3>::TOTAL : PairLayout<192, 4>::TOTAL;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cudaError_t e = pbn == 256 ? cudaLaunchKernelEx(&cfg, k_tc_gemm_pair<256, 3>, ma, mbh, p)
-                                   : cudaLaunchKernelEx(&cfg, k_tc_gemm_pair<192, 4>, ma, mbh, p);
-        if (e != cudaSuccess) return check_cuda(c, e, "pair GEMM launch");
-        c->launches++;
-    } else if (wide) {
-        APF_LAUNCH(c, (k_tc_gemm<256, 4>), grid, 192, smem_wide, s, ma, mb, p);
-    } else {
-        APF_LAUNCH(c, (k_tc_gemm<128, 6>), grid, 192, smem_narrow, s, ma, mb, p);
+        kind = pbn == 256 ? 2 : 3;
+        long long ntp = (long long)nprob * ((M + 2 * BM - 1) / (2 * BM)) * ((N + pbn - 1) / pbn);
+        grid = (unsigned)(2 * std::min<long long>(ntp, pair_slots));
     }
+    int pi = -1;
+    if (c->prof_on && 2 * (c->prof_used + 1) <= (int)c->prof_ev.size()) {
+        pi = c->prof_used++;
+        // complex m x k x n product: M = m, N = 2n, kp ~ 2k real
+        double alg = 2.0 * (double)M * (double)N * (double)kp * nprob;
+        c->prof_alg[pi] = alg;
+        c->prof_hw[pi] = alg * p.nseg;
+        record_event(c, c->prof_ev[2 * pi], s);
+    }
+    int rc = nprob == 1 ? launch_variant<1>(c, kind, 1, pb, p, grid, s)
+                        : launch_variant<TC_MAX_BATCH>(c, kind, nprob, pb, p, grid, s);
+    if (rc != APF_OK) return rc;
     if (pi >= 0) record_event(c, c->prof_ev[2 * pi + 1], s);
     return APF_OK;
+}
+
+int tc_gemm(apf_ctx *c, const PackView &A, const PackView &B, int nsplit, int M, int N, int n_cplx, float alpha,
+            float beta, float *out_re, float *out_im, long long ldo, const float *in_re, const float *in_im,
+            long long ldi, cudaStream_t s) {
+    TcProblem pb{A, B, out_re, out_im, in_re, in_im, c->d_flags};
+    return tc_gemm_n(c, 1, &pb, nsplit, M, N, n_cplx, alpha, beta, ldo, ldi, s);
 }

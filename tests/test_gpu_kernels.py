@@ -56,8 +56,10 @@ def test_tc_cgemm_against_torch(env, shape, nsplit):
 
 
 # leaf = block size + 1000 * leaf kernel variant (128 blocks: 0 in-CTA Schur
-# recursion over 32 x 32 Gauss-Jordan leaves, 3 single-level Gauss-Jordan)
-@pytest.mark.parametrize("n,leaf", [(64, 64), (256, 64), (128, 128), (512, 128), (1024, 128), (1024, 3128)])
+# recursion over 32 x 32 Gauss-Jordan leaves, 3 single-level Gauss-Jordan);
+# + 100000: through the symmetric random butterfly transform
+@pytest.mark.parametrize("n,leaf", [(64, 64), (256, 64), (128, 128), (512, 128), (1024, 128), (1024, 3128),
+                                    (512, 100128), (2048, 100128)])
 def test_mixed_recursive_inverse(env, n, leaf):
     """Inverse of a complex-symmetric matrix shaped like a slab Schur block
     (diagonal ~4 - k^2 eps, periodic -1 neighbours, a dense symmetric

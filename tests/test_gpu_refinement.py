@@ -84,3 +84,26 @@ def test_set_krylov_arguments_and_reallocation(apf):
     with pytest.raises(apf.APFError) as ei:
         s64.set_krylov(2)
     assert ei.value.code == apf.APF_EINVAL
+
+
+@pytest.mark.parametrize("planes,butterfly", [(3, False), (2, True), (3, True)])
+def test_elimination_options_against_golden(planes, butterfly):
+    """The elimination options (bf16x6 products, the symmetric random
+    butterfly transform of the slab blocks) change only the approximate
+    factorization: after refinement S and grad f match the stored oracle
+    values on the 1024 x 240 grid at the mixed-mode tolerances."""
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2306_09257_gb300 import apf, build
+    from paper_2306_09257_gb300 import workloads as W
+    build.build_lib()
+    ref = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mid_1024x240_seed0.npz"))
+    w = W.MID
+    s = apf.solver_for_workload(w, w.eps_slab(0), precision="mixed")
+    s.set_elimination(planes, butterfly)
+    S, f, g = s.solve_S_grad("splitter", [-2, -1, 0, 1, 2], 0.18)
+    assert np.linalg.norm(S - ref["S"]) / np.linalg.norm(ref["S"]) <= 1e-6
+    assert np.linalg.norm(g - ref["grad"]) / np.linalg.norm(ref["grad"]) <= 1e-5
+    assert s.stats()["residual"] <= 1e-10

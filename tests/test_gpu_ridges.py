@@ -158,3 +158,24 @@ def test_ridge_argument_errors(apf):
         with pytest.raises(apf.APFError) as ei:
             s.set_ridges(np.array(bad), w.h, 4.0, 1.0, w.eps_sub, w.eps_clad, mirror=mirror)
         assert ei.value.code == apf.APF_EINVAL
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_high_contrast_ridges_converge_at_defaults(apf, seed):
+    """Amorphous-silicon ridges (eps 13.69, the paper's Sec. 3 material) in
+    air on silica, 1024 x 240: the mixed path at the library's default
+    refinement (tolerance 1e-10, 40 sweeps) converges (no APF_ENOCONV) and
+    agrees with the float64 path."""
+    w = W.MID
+    e = W.ridge_edges(w.nx, W.ridge_count(w), seed, mirror=True)
+    out = {}
+    for prec in ("mixed", "fp64"):
+        s = grid_solver(apf, w, prec)
+        s.set_ridges(e, w.h, 13.69, 1.0, w.eps_sub, w.eps_clad, mirror=True, j0=w.j0, eps_out=False)
+        s.set_channels(None, None)
+        out[prec] = s.solve_S_grad("splitter", ORDERS, 0.18)
+        if prec == "mixed":
+            st = s.stats()
+            assert st["residual"] <= 1e-10 and st["refine_iters"] <= 40, st
+    assert rel(out["mixed"][0], out["fp64"][0]) <= 1e-8
+    assert rel(out["mixed"][2], out["fp64"][2]) <= 1e-5
