@@ -73,9 +73,13 @@ def args_parse():
                    help="batch: the designs share every launch (apf_solve_S_grad_batch, one stream); streams: one "
                         "host thread + stream per design, one design per call")
     p.add_argument("--no-compare", action="store_true", help="skip timing the other --mode for comparison")
+    p.add_argument("--groups", type=int, default=1,
+                   help="batch mode: the designs form this many batched calls, each on its own thread and stream, "
+                        "so one group's latency-bound steps overlap another group's tensor-core work")
     p.add_argument("--planes", type=int, default=2, choices=[2, 3],
                    help="bf16 split planes of the mixed elimination (3: bf16x6, for high-contrast slabs)")
-    p.add_argument("--butterfly", action="store_true", help="random butterfly transform of the slab blocks")
+    p.add_argument("--no-butterfly", action="store_true",
+                   help="switch off the random butterfly transform of the slab blocks (on by default)")
     return p.parse_args()
 
 
@@ -321,8 +325,8 @@ def main():
         sv.set_channels(None, None)
         if prec == "mixed":
             sv.set_refinement(a.refine_tol, 40)
-            if a.planes != 2 or a.butterfly:
-                sv.set_elimination(a.planes, a.butterfly)
+            if a.planes != 2 or a.no_butterfly:
+                sv.set_elimination(a.planes, not a.no_butterfly)
         return sv
 
     solvers = [new_solver("mixed", x_host[b][0]) for b in range(B)]
@@ -381,31 +385,59 @@ def main():
         if errors:
             raise errors[0]
 
-    def step_batch_dev(i):
-        """One batched call: all B designs' S + grad f in shared launches."""
-        for b in range(B):
+    G = max(1, min(a.groups, B))
+    groups = [list(range(gi, B, G)) for gi in range(G)]  # designs of each batched call
+
+    def step_batch_dev(i, grp=None):
+        """One batched call: the group's designs' S + grad f in shared launches."""
+        grp = list(range(B)) if grp is None else grp
+        for b in grp:
             set_design(solvers[b], x_dev[b][i % nseeds])
-        apf.solve_S_grad_batch(solvers, "splitter", ORDERS, TARGET, out_S=S_d, out_grad=g_d)
+        apf.solve_S_grad_batch([solvers[b] for b in grp], "splitter", ORDERS, TARGET,
+                               out_S=[S_d[b] for b in grp], out_grad=[g_d[b] for b in grp])
         if ridges:
-            for b in range(B):
+            for b in grp:
                 solvers[b].ridge_grad(g_d[b], out=ge_d[b])
 
-    def step_batch_host(i):
-        for b in range(B):
+    def step_batch_host(i, grp=None):
+        grp = list(range(B)) if grp is None else grp
+        for b in grp:
             set_design(solvers[b], x_host[b][i % nseeds])
+        sv = [solvers[b] for b in grp]
         if ridges:
-            apf.solve_S_grad_batch(solvers, "splitter", ORDERS, TARGET, out_grad=g_d)
-            for b in range(B):
+            apf.solve_S_grad_batch(sv, "splitter", ORDERS, TARGET, out_grad=[g_d[b] for b in grp])
+            for b in grp:
                 solvers[b].ridge_grad(g_d[b])
         else:
-            apf.solve_S_grad_batch(solvers, "splitter", ORDERS, TARGET)
+            apf.solve_S_grad_batch(sv, "splitter", ORDERS, TARGET)
 
-    def record_stats():
-        for b in range(B):
-            st = solvers[b].stats()
-            stats_acc[b]["launches"] += st["kernel_launches"]
-            stats_acc[b]["iters"].append(st["refine_iters"])
-            stats_acc[b]["fallbacks"] += st["leaf_fallbacks"]
+    def run_groups(fn, nsteps, start_ev=None, end_evs=None, record=False):
+        """Each group's batched calls on its own host thread and stream."""
+        def worker(gi):
+            try:
+                with torch.cuda.stream(streams[gi]):
+                    if start_ev is not None:
+                        streams[gi].wait_event(start_ev)
+                    for i in range(nsteps):
+                        fn(i, groups[gi])
+                        if record:
+                            for b in groups[gi]:
+                                st = solvers[b].stats()
+                                stats_acc[b]["launches"] += st["kernel_launches"]
+                                stats_acc[b]["iters"].append(st["refine_iters"])
+                                stats_acc[b]["fallbacks"] += st["leaf_fallbacks"]
+                    if end_evs is not None:
+                        for b in groups[gi]:
+                            end_evs[b].record(streams[gi])
+            except BaseException as e:
+                errors.append(e)
+        ths = [threading.Thread(target=worker, args=(gi,)) for gi in range(G)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        if errors:
+            raise errors[0]
 
     def timed(run_steps, nsteps, sample_clocks=False):
         """Device time of nsteps (events on the main stream, fenced against every
@@ -431,14 +463,7 @@ def main():
         return replicas.max_over_ranks(e0.elapsed_time(e1)), (clk.stop() if clk else None)
 
     def batch_steps(nsteps, start_ev, end_evs, record=False):
-        with torch.cuda.stream(streams[0]):
-            streams[0].wait_event(start_ev)
-            for i in range(nsteps):
-                step_batch_dev(i)
-                if record:
-                    record_stats()
-            for ev in end_evs:
-                ev.record(streams[0])
+        run_groups(step_batch_dev, nsteps, start_ev, end_evs, record=record)
 
     def stream_steps(nsteps, start_ev, end_evs, record=False):
         run_all(step_dev, nsteps, start_ev, end_evs, record=record)
@@ -446,9 +471,7 @@ def main():
     batched = a.mode == "batch" and B > 1
     # ---- 1. the headline: B designs in flight, inputs resident on the device ----
     if batched:
-        with torch.cuda.stream(streams[0]):
-            for i in range(a.warmup):
-                step_batch_dev(i)
+        run_groups(step_batch_dev, a.warmup)
         ms, clocks = timed(lambda n, e, ev: batch_steps(n, e, ev, record=True), a.steps, sample_clocks=True)
     else:
         run_all(step_dev, a.warmup)
@@ -466,11 +489,10 @@ def main():
             other = {"mode": f"{B} host threads, one context + stream each, one design per call",
                      "value": replicas.whole_job_throughput(ws, B, a.steps, ms_o), "unit": "evals/s"}
         else:
-            with torch.cuda.stream(streams[0]):
-                step_batch_dev(0)
+            run_groups(step_batch_dev, 1)
             ms_o, _ = timed(lambda n, e, ev: batch_steps(n, e, ev), a.steps)
-            other = {"mode": f"apf_solve_S_grad_batch, {B} designs per call", "unit": "evals/s",
-                     "value": replicas.whole_job_throughput(ws, B, a.steps, ms_o)}
+            other = {"mode": f"apf_solve_S_grad_batch, {G} group(s) of {len(groups[0])} designs per call",
+                     "unit": "evals/s", "value": replicas.whole_job_throughput(ws, B, a.steps, ms_o)}
 
     # ---- 2. end to end at the same concurrency and step count: host buffers ----
     torch.cuda.synchronize()
@@ -478,9 +500,7 @@ def main():
         dist.barrier()
     t0 = time.perf_counter()
     if batched:
-        with torch.cuda.stream(streams[0]):
-            for i in range(a.steps):
-                step_batch_host(i)
+        run_groups(step_batch_host, a.steps)
     else:
         run_all(step_host, a.steps)
     torch.cuda.synchronize()
@@ -681,8 +701,9 @@ def main():
                            "refine_iters": iters, "residual": st_last["residual"],
                            "leaf_fallbacks_per_step": sum(x["fallbacks"] for x in stats_acc) / (B * a.steps),
                            "concurrent_designs_per_gpu": B, "elimination_planes": a.planes,
-                           "butterfly": bool(a.butterfly),
-                           "mode": ("apf_solve_S_grad_batch: B designs share every launch" if batched else
+                           "butterfly": not a.no_butterfly,
+                           "mode": (f"apf_solve_S_grad_batch: {G} group(s) of {len(groups[0])} designs, each group "
+                                    f"sharing every launch, one thread + stream per group" if batched else
                                     "one host thread + stream per design"),
                            "parallelism": f"replicas x{ws}, {B} independent designs per GPU"},
                 "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -292,13 +292,14 @@ int apf_set_schur_storage(apf_ctx *ctx, int segment_rows);
    tensor work of the elimination and 1.5 times the storage of the packed
    inverses.  High-contrast slabs (e.g. silicon ridges in air) make the slab
    Schur blocks ill-conditioned; their refinement can stall with two planes
-   and converges with three.  butterfly = 1 applies a symmetric random
-   butterfly transform (depth 2) to every slab block before its inversion
-   (G = U (U^T X U)^-1 U^T), which spreads the rows of strongly structured
-   blocks so that the recursion, which pivots only inside its 32 x 32 leaves,
-   meets no nearly singular leading block.  Re-creates the workspace like
-   apf_set_krylov.  APF_EINVAL for other values, or in APF_FP64 mode for
-   anything but (2, 0). */
+   and converges with three.  butterfly = 1 (the mixed-mode default) applies
+   a symmetric random butterfly transform (depth 2) to every slab block before
+   its inversion (G = U (U^T X U)^-1 U^T), which spreads the rows of strongly
+   structured blocks so that the recursion, which pivots only inside its
+   32 x 32 leaves, meets no nearly singular leading block: with it the same
+   high-contrast slabs converge with two planes, for two memory-bound passes
+   over each slab block.  Re-creates the workspace like apf_set_krylov.
+   APF_EINVAL for other values, or in APF_FP64 mode for anything but (2, 0). */
 int apf_set_elimination(apf_ctx *ctx, int planes, int butterfly);
 
 /* Measurement support (no counterpart in the paper).  When enabled, every

@@ -276,7 +276,7 @@ class Solver:
         self._check(self._L.apf_set_schur_storage(self._h, int(segment_rows)))
         self.version += 1
 
-    def set_elimination(self, planes: int = 2, butterfly: bool = False):
+    def set_elimination(self, planes: int = 2, butterfly: bool = True):
         """Mixed mode: bf16 split planes of the elimination (2: bf16x3, 3:
         bf16x6) and the symmetric random butterfly transform of the slab
         blocks (see apf_set_elimination)."""

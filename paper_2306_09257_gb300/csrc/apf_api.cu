@@ -13,12 +13,21 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 
 
 static char g_create_err[512] = "no error";
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("APF_PDL");  // diagnostic knob; default off (measured slower, see DESIGN)
+        return e && e[0] == '1';
+    }();
+    return on;
+}
 
 int set_err(apf_ctx *c, int code, const char *fmt, ...) {
     char buf[512];
@@ -166,6 +175,7 @@ int apf_create(apf_ctx **out, int cuda_device, int precision) {
     apf_ctx *c = new apf_ctx();
     c->device = cuda_device;
     c->precision = precision;
+    c->butterfly = precision == APF_MIXED_BF16X3 ? 1 : 0;  // see apf_set_elimination
     for (auto &ev : c->ev) cudaEventCreate(&ev);
     cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     slab64_init_attrs();

@@ -223,6 +223,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcAr
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
     int issued = 0;
+    // set-up done; global memory only after the preceding kernel has completed
+    pdl_wait();
+    pdl_launch_dependents();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -442,6 +445,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
     int issued = 0;
+    // set-up done; global memory only after the preceding kernel has completed
+    pdl_wait();
+    pdl_launch_dependents();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -651,23 +657,27 @@ namespace {
 
 template <int P, typename K>
 cudaError_t launch_args(apf_ctx *c, K kern, bool pair, unsigned grid, int smem, cudaStream_t s, const TcArgs<P> &args) {
-    if (!pair) {
-        kern<<<grid, 192, smem, s>>>(args);
-        c->launches++;
-        return cudaSuccess;
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(192);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    if (pair) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = 2;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    if (pdl_enabled()) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = na;
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args);
     if (e == cudaSuccess) c->launches++;
     return e;
