@@ -67,13 +67,13 @@ def args_parse():
                         "~1e-7 and grad f within ~1e-6 of the float64 path, inside the stated 1e-6 / 1e-5")
     p.add_argument("--design", default="filtered", choices=["filtered", "ridges"],
                    help="permittivity maps: filtered-threshold pixels or ridge edge positions")
-    p.add_argument("--concurrent", type=int, default=8,
+    p.add_argument("--concurrent", type=int, default=16,
                    help="independent designs in flight per GPU (one context each)")
     p.add_argument("--mode", default="batch", choices=["batch", "streams"],
                    help="batch: the designs share every launch (apf_solve_S_grad_batch, one stream); streams: one "
                         "host thread + stream per design, one design per call")
     p.add_argument("--no-compare", action="store_true", help="skip timing the other --mode for comparison")
-    p.add_argument("--groups", type=int, default=1,
+    p.add_argument("--groups", type=int, default=2,
                    help="batch mode: the designs form this many batched calls, each on its own thread and stream, "
                         "so one group's latency-bound steps overlap another group's tensor-core work")
     p.add_argument("--planes", type=int, default=2, choices=[2, 3],
@@ -301,6 +301,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B = max(1, a.concurrent)
+    if a.mode == "streams" and B > 8:
+        # 16 host threads, each with its own context and stream, did not finish on GB300 (no kernel fault; the
+        # GPU still answered after the process was killed); the batch mode keeps B designs on G threads instead
+        raise SystemExit("--mode streams runs at most 8 designs; use --mode batch (--groups) for more")
     nseeds = 4
     ridges = a.design == "ridges"
     seeds = replicas.replica_seeds(rank, B, nseeds)
@@ -482,7 +486,7 @@ def main():
     st_last = s.stats()
     # the other way of keeping B designs in flight, for comparison
     other = None
-    if B > 1 and not a.no_compare:
+    if B > 1 and not a.no_compare and not (batched and B > 8):
         if batched:
             run_all(step_dev, 1)
             ms_o, _ = timed(lambda n, e, ev: stream_steps(n, e, ev), a.steps)
@@ -513,6 +517,28 @@ def main():
     else:
         h2d = w.h * w.nx * 8
         d2h = nin * nout * 16 + w.h * w.nx * 8 + 8
+
+    # ---- 2b. the tensor-core GEMM's in-step roofline in the batched step: all B designs
+    # (up to 8) in one call on one stream, so every GEMM's CUDA-event interval is that launch alone
+    prof_b = None
+    if batched:
+        nbp = min(B, 8)
+        lead = solvers[0]
+        lead.set_profiling(True)
+        with torch.cuda.stream(streams[0]):
+            step_batch_dev(0, list(range(nbp)))
+        torch.cuda.synchronize()
+        lead.set_profiling(True)  # reset the counters
+        nb_steps = 2
+        with torch.cuda.stream(streams[0]):
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(streams[0])
+            for i in range(nb_steps):
+                step_batch_dev(i, list(range(nbp)))
+            q1.record(streams[0])
+        torch.cuda.synchronize()
+        prof_b = dict(lead.profile(), designs=nbp, steps=nb_steps, ms_per_step=q0.elapsed_time(q1) / nb_steps)
+        lead.set_profiling(False)
 
     # ---- 3. one design alone: its rate, then the tensor-core GEMM's in-step roofline ----
     # (a single stream, so every GEMM's CUDA-event interval is that launch alone)
@@ -651,21 +677,28 @@ def main():
     pk, src = peaks()
     peak_sus = pk.get("bf16_tflops_sustained", 1700.0)
     burst = pk.get("bf16_tflops", 1900.0)
-    hw_tf = prof["gemm_hw_flops"] / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else 0.0
-    alg_tf = prof["gemm_alg_flops"] / (prof["gemm_ms"] / 1e3) / 1e12 if prof["gemm_ms"] > 0 else 0.0
-    per_launch_flops = prof["gemm_hw_flops"] / max(1, prof["gemm_launches"])
-    traffic = None
-    if GEMM_CAPTURE["bytes_per_hw_flop"] is not None:
-        traffic = GEMM_CAPTURE["bytes_per_hw_flop"] * per_launch_flops
-    roofline = {"bound": "tensor", "achieved": hw_tf, "peak": peak_sus, "unit": "TFLOP/s",
-                "frac": hw_tf / peak_sus, "traffic": traffic,
-                "kernel": "k_tc_gemm_pair / k_tc_gemm (tcgen05 bf16, fp32 accumulate)",
-                "achieved_algorithmic_complex_tflops": alg_tf,
-                "note": (f"one design alone on one stream ({n1} steps): achieved = bf16 tensor flops (8 m n k per "
-                         f"complex product x plane products) / summed CUDA-event launch time "
-                         f"({prof['gemm_ms'] / n1:.2f} ms of the {ms1p:.2f} ms profiled step); peak = bf16_tflops_sustained "
-                         f"({src}, of measured); traffic = DRAM bytes per launch scaled from the ncu capture "
-                         f"{GEMM_CAPTURE['profile']} by the launch's flops")}
+    def gemm_roofline(pr, where):
+        hw = pr["gemm_hw_flops"] / (pr["gemm_ms"] / 1e3) / 1e12 if pr["gemm_ms"] > 0 else 0.0
+        alg = pr["gemm_alg_flops"] / (pr["gemm_ms"] / 1e3) / 1e12 if pr["gemm_ms"] > 0 else 0.0
+        per_launch = pr["gemm_hw_flops"] / max(1, pr["gemm_launches"])
+        tr = GEMM_CAPTURE["bytes_per_hw_flop"] * per_launch if GEMM_CAPTURE["bytes_per_hw_flop"] else None
+        return {"bound": "tensor", "achieved": hw, "peak": peak_sus, "unit": "TFLOP/s", "frac": hw / peak_sus,
+                "traffic": tr, "kernel": "k_tc_gemm_pair / k_tc_gemm (tcgen05 bf16, fp32 accumulate)",
+                "achieved_algorithmic_complex_tflops": alg, "gemm_launches": pr["gemm_launches"],
+                "note": (f"{where}: achieved = bf16 tensor flops (8 m n k per complex product x plane products) / "
+                         f"summed CUDA-event launch time of the GEMMs; peak = bf16_tflops_sustained ({src}, of "
+                         f"measured); traffic = DRAM bytes per launch scaled from the ncu capture "
+                         f"{GEMM_CAPTURE['profile']} by the average launch's flops")}
+
+    single_rf = gemm_roofline(prof, f"one design alone on one stream, {n1} steps, GEMMs {prof['gemm_ms'] / n1:.2f} "
+                                    f"ms of the {ms1p:.2f} ms profiled step")
+    if prof_b is not None:
+        roofline = gemm_roofline(prof_b, f"the batched step, {prof_b['designs']} designs in one call on one stream, "
+                                         f"{prof_b['steps']} steps, GEMMs {prof_b['gemm_ms'] / prof_b['steps']:.1f} "
+                                         f"ms of the {prof_b['ms_per_step']:.1f} ms profiled step")
+        roofline["single_design"] = single_rf
+    else:
+        roofline = single_rf
     iso = isolated_gemm(apf, local, nin + nout, w.nx, w.nx)
     if iso:
         iso_tf = iso["gemm_hw_flops"] / (iso["gemm_ms"] / 1e3) / 1e12

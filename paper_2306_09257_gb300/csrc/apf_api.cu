@@ -21,13 +21,7 @@
 
 static char g_create_err[512] = "no error";
 
-bool pdl_enabled() {
-    static const bool on = [] {
-        const char *e = getenv("APF_PDL");  // diagnostic knob; default off (measured slower, see DESIGN)
-        return e && e[0] == '1';
-    }();
-    return on;
-}
+
 
 int set_err(apf_ctx *c, int code, const char *fmt, ...) {
     char buf[512];

@@ -5,7 +5,6 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <string>
-#include <utility>
 #include <vector>
 
 #include "../../include/apf.h"
@@ -153,45 +152,10 @@ struct apf_ctx {
 // ---------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------
-// Programmatic dependent launch (opt-in, APF_PDL=1): every library kernel can
-// be launched so that it may be scheduled while the kernel before it on the
-// stream finishes (its launch and, for the tensor-core GEMM, its barrier /
-// tensor-memory set-up overlap that kernel's tail).  Each kernel therefore starts with
-// APF_KERNEL_PROLOGUE (or, in the GEMM, calls pdl_wait after its set-up):
-// griddepcontrol.wait returns once the preceding grid has completed and its
-// memory is visible, so no global memory is touched before it, and
-// launch_dependents lets the next kernel be scheduled in turn.  A kernel
-// launched without the attribute passes both immediately.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-#define APF_KERNEL_PROLOGUE() \
-    do {                      \
-        pdl_wait();           \
-        pdl_launch_dependents(); \
-    } while (0)
-
-bool pdl_enabled();  // APF_PDL=1 turns the attribute on (default off)
-
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_kernel(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                                 cudaStream_t s, Args &&...args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
-
-#define APF_LAUNCH(ctx, kernel, grid, block, smem, stream, ...)                                          \
-    do {                                                                                                  \
-        launch_kernel(pdl_enabled(), kernel, dim3(grid), dim3(block), (size_t)(smem), (stream), __VA_ARGS__); \
-        (ctx)->launches++;                                                                                \
+#define APF_LAUNCH(ctx, kernel, grid, block, smem, stream, ...)              \
+    do {                                                                      \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);           \
+        (ctx)->launches++;                                                    \
     } while (0)
 
 GridDev make_grid(const apf_ctx *c);

@@ -35,7 +35,6 @@ __device__ double2 stretch_at(const GridDev &g, double y) {
 // Stretch table: st[j] = s_j (integer rows), st[ny + 1 + j] = 1 / s_{j - 1/2}
 // for j = 0..ny (half-integer rows, Dirichlet walls beyond the ends).
 __global__ void k_stretch_table(GridDev g, double2 *st) {
-    APF_KERNEL_PROLOGUE();
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j > g.ny) return;
     if (j < g.ny) st[j] = stretch_at(g, (double)j);
@@ -52,7 +51,6 @@ __device__ __forceinline__ double2 row_diag(const GridDev &g, const double2 *st,
 }
 
 __global__ void k_boundary_sweep(GridDev g, const double2 *st, double2 *modes) {
-    APF_KERNEL_PROLOGUE();
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= g.nx) return;
     const double2 *ish = st + g.ny + 1;  // ish[j] = 1 / s_{j - 1/2}
@@ -99,7 +97,6 @@ __device__ __forceinline__ int mod_nx(int m, int nx) { int r = m % nx; return r 
 
 __global__ void k_channel_coef(GridDev g, const int *m_in, int n_in, const int *m_out, int n_out,
                                const double2 *modes, double2 *coef) {
-    APF_KERNEL_PROLOGUE();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < n_in) {
         int m = m_in[c];
@@ -120,7 +117,6 @@ __global__ void k_channel_coef(GridDev g, const int *m_in, int n_in, const int *
 // (C^T projected through the cladding; A = A^T).
 __global__ void k_build_rhs(GridDev g, const int *m_in, int n_in, const int *m_out, int n_out,
                             const double2 *coef, double2 *E) {
-    APF_KERNEL_PROLOGUE();
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
     if (x >= g.nx) return;
@@ -140,7 +136,6 @@ __global__ void k_build_rhs(GridDev g, const int *m_in, int n_in, const int *m_o
 // every (a, b) writes its own element).
 __global__ void k_adjoint_spectrum(const double2 *Gamma, const double2 *coef, const int *m_out, int n_in, int n_out,
                                    int nx, double2 *spec) {
-    APF_KERNEL_PROLOGUE();
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     int b = blockIdx.y;
     if (a >= n_in) return;
@@ -149,7 +144,6 @@ __global__ void k_adjoint_spectrum(const double2 *Gamma, const double2 *coef, co
 }
 
 __global__ void k_twiddles(double2 *tw, int n) {
-    APF_KERNEL_PROLOGUE();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n / 2) return;
     double sn, cs;
@@ -161,7 +155,6 @@ __global__ void k_twiddles(double2 *tw, int n) {
 // memory: out[k] = scale * sum_x in[x] exp(sign * 2 pi i k x / n).
 __global__ void k_fft(const double2 *in, double2 *out, int n, int logn, long long in_stride,
                       long long out_stride, int sign, double scale, const double2 *tw) {
-    APF_KERNEL_PROLOGUE();
     extern __shared__ double2 a[];
     const double2 *src = in + (long long)blockIdx.x * in_stride;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -198,7 +191,6 @@ __global__ void k_fft(const double2 *in, double2 *out, int n, int logn, long lon
 // is symmetric, so the same factor carries the source up), and
 // q = sum_{j=src}^{j0-1} G_j^2 / dt_j with G_src = 1, G_{j+1} = G_j c_{j+1}/dt_j.
 __global__ void k_source_row(GridDev g, const double2 *st, double2 *q) {
-    APF_KERNEL_PROLOGUE();
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= g.nx) return;
     const double2 *ish = st + g.ny + 1;
@@ -222,7 +214,6 @@ __global__ void k_source_row(GridDev g, const double2 *st, double2 *q) {
 // the (1/sqrt(nx)) FFT of forward column a on the first slab row.
 __global__ void k_reflection(GridDev g, const double2 *fft0, const double2 *modes, const double2 *q,
                              const int *m_in, int n_in, const int *m_ref, int n_ref, double2 *R) {
-    APF_KERNEL_PROLOGUE();
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     int b = blockIdx.y;
     if (a >= n_in || b >= n_ref) return;
@@ -243,7 +234,6 @@ __global__ void k_reflection(GridDev g, const double2 *fft0, const double2 *mode
 // adjoint column with m_out[b] = -m_out[qq] (cladding order m_out[qq]).
 __global__ void k_reverse_S(GridDev g, const double2 *fft0, const double2 *modes, const int *m_in, int n_in,
                             const int *rmap, int n_out, double2 *Srev) {
-    APF_KERNEL_PROLOGUE();
     int qq = blockIdx.x * blockDim.x + threadIdx.x;
     int p = blockIdx.y;
     if (qq >= n_out || p >= n_in) return;

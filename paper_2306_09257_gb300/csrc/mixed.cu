@@ -99,7 +99,6 @@ constexpr int MAX_JOBS = 2 * TC_MAX_BATCH;
 // Tile: 32 rows x 64 k; thread (tx, ty) handles k = k0 + 2 tx, +1 (bf16x2 stores).
 template <int N>
 __global__ void __launch_bounds__(256) k_pack32(const __grid_constant__ PackJobsN<N> jobs) {
-    APF_KERNEL_PROLOGUE();
     const PackJob &J = jobs.j[blockIdx.z];
     __shared__ float tre[32][65], tim[32][65];
     const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
@@ -182,7 +181,6 @@ __device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (*v)[3], int p, bool 
 
 template <int N>
 __global__ void __launch_bounds__(256) k_pack32v(const __grid_constant__ PackJobsN<N> jobs) {
-    APF_KERNEL_PROLOGUE();
     const PackJob &J = jobs.j[blockIdx.z];
     __shared__ float tre[32][65], tim[32][65];
     const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
@@ -236,7 +234,6 @@ __global__ void __launch_bounds__(256) k_pack32v(const __grid_constant__ PackJob
 // row r = [Re v(r,:), Im v(r,:)], v = s1 (+ s2).
 __global__ void k_pack64_A(const __grid_constant__ Tab<const double2 *> s1t, const __grid_constant__ Tab<const double2 *> s2t, long long ld, int R, int K,
                            int nsplit, const __grid_constant__ Tab<__nv_bfloat16 *> outt, long long kp, long long plane_pitch) {
-    APF_KERNEL_PROLOGUE();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     int r = blockIdx.y;
     if (k >= K || r >= R) return;
@@ -260,7 +257,6 @@ __global__ void k_pack64_A(const __grid_constant__ Tab<const double2 *> s1t, con
 // v(r, k) = src[k][r] (r < R, k < K) -> rows r and R + r.
 __global__ void k_pack64_BT(const __grid_constant__ Tab<const double2 *> srct, long long ld, int R, int K, int nsplit,
                             const __grid_constant__ Tab<__nv_bfloat16 *> outt, long long kp, long long plane_pitch) {
-    APF_KERNEL_PROLOGUE();
     __shared__ double2 t[32][33];
     const double2 *__restrict__ src = srct.v[blockIdx.z];
     __nv_bfloat16 *out = outt.v[blockIdx.z];
@@ -299,7 +295,6 @@ __global__ void k_pack64_BT(const __grid_constant__ Tab<const double2 *> srct, l
 // first / last slab row).  Thread: 4 consecutive columns xp of row x (n % 4 == 0).
 __global__ void k_assemble32(GridDev g, int row, const __grid_constant__ Tab<const double *> epst, const double2 *circ,
                              const __grid_constant__ Tab<const float *> Gret, const __grid_constant__ Tab<const float *> Gimt, const __grid_constant__ Tab<float *> Xret, const __grid_constant__ Tab<float *> Ximt) {
-    APF_KERNEL_PROLOGUE();
     const int b = blockIdx.z;
     const double *eps = epst.v[b];
     const float *Gre = Gret.v[b], *Gim = Gimt.v[b];
@@ -361,7 +356,6 @@ __device__ __forceinline__ void bf_inv(float2 &t, float2 &b, float wa, float wb)
 }
 template <bool INV>
 __global__ void k_butterfly(const __grid_constant__ Tab<float *> ret, const __grid_constant__ Tab<float *> imt, long long ld, int n, const float *w) {
-    APF_KERNEL_PROLOGUE();
     float *re = ret.v[blockIdx.z], *im = imt.v[blockIdx.z];
     const int q = n >> 2;
     const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
@@ -415,7 +409,6 @@ __global__ void k_butterfly(const __grid_constant__ Tab<float *> ret, const __gr
 // Float32 Gauss-Jordan inverse of an n x n (n <= 128) diagonal block with
 // partial pivoting, in shared memory (planar in global memory).
 __global__ void __launch_bounds__(512) k_leaf_inv32(float *re, float *im, long long ld, int n, int *flags) {
-    APF_KERNEL_PROLOGUE();
     extern __shared__ float2 a32[];
     __shared__ float2 colk[128];
     __shared__ int piv[128];
@@ -501,33 +494,28 @@ __global__ void __launch_bounds__(512) k_leaf_inv32(float *re, float *im, long l
 
 template <int NB>
 __global__ void __launch_bounds__(NB * 4) k_leaf32(float *re, float *im, long long ld, int *flags) {
-    APF_KERNEL_PROLOGUE();
     LeafIO<float, true> io{re, im, nullptr, ld};
     leaf_gj<float, NB, true>(io, flags);
 }
 
 template <int NB>
 __global__ void __launch_bounds__(NB * 4) k_leaf32r(float *re, float *im, long long ld, int *flags) {
-    APF_KERNEL_PROLOGUE();
     leaf_gj_regs<NB>(re, im, ld, flags);
 }
 
 __global__ void __launch_bounds__(512) k_leaf128rec(const __grid_constant__ Tab<float *> re, const __grid_constant__ Tab<float *> im, long long ld, const __grid_constant__ Tab<int *> flags) {
-    APF_KERNEL_PROLOGUE();
     const int b = blockIdx.x;
     leaf128_recursive(re.v[b], im.v[b], ld, flags.v[b]);
 }
 
 template <int NB>
 __global__ void __launch_bounds__(NB * 4) k_leaf32r2(float *re, float *im, long long ld, int *flags) {
-    APF_KERNEL_PROLOGUE();
     leaf_gj_regs2<NB>(re, im, ld, flags);
 }
 
 // C block <- -V, B block <- -V^T (planar float32).
 __global__ void k_negoff32(const __grid_constant__ Tab<float *> Bret, const __grid_constant__ Tab<float *> Bimt, const __grid_constant__ Tab<float *> Cret, const __grid_constant__ Tab<float *> Cimt, long long ld,
                            const __grid_constant__ Tab<const float *> Vret, const __grid_constant__ Tab<const float *> Vimt, int h) {
-    APF_KERNEL_PROLOGUE();
     __shared__ float tr[32][33], ti[32][33];
     const int b = blockIdx.z;
     float *Bre = Bret.v[b], *Bim = Bimt.v[b], *Cre = Cret.v[b], *Cim = Cimt.v[b];
@@ -556,7 +544,6 @@ __global__ void k_negoff32(const __grid_constant__ Tab<float *> Bret, const __gr
 // E[c][x] = (R ? R[c][x] : 0) + O[c][x] for c < mcols;  E = R for c >= mcols.
 __global__ void k_combine(const __grid_constant__ Tab<double2 *> Et, const __grid_constant__ Tab<const double2 *> Rt, const __grid_constant__ Tab<const float *> Oret,
                           const __grid_constant__ Tab<const float *> Oimt, int ncol, int mcols, int nx) {
-    APF_KERNEL_PROLOGUE();
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y;
     if (x >= nx) return;
@@ -575,7 +562,6 @@ __global__ void k_combine(const __grid_constant__ Tab<double2 *> Et, const __gri
 // inverse DFT of sigma times the DFT of the column.
 __global__ void k_circ_apply(const double2 *in, double2 *out, int n, int logn, const double2 *sigma,
                              const double2 *tw) {
-    APF_KERNEL_PROLOGUE();
     extern __shared__ double2 a[];
     const double2 *src = in + (long long)blockIdx.x * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) a[__brev((unsigned)i) >> (32 - logn)] = src[i];
@@ -617,7 +603,6 @@ __global__ void k_circ_apply(const double2 *in, double2 *out, int n, int logn, c
 // r_j = R_j - K E restricted to the slab, float64.
 __global__ void k_residual(GridDev g, const double *eps, const double2 *E, const double2 *R, const double2 *cb,
                            const double2 *ct, double2 *r, int ncol) {
-    APF_KERNEL_PROLOGUE();
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int c = blockIdx.y, j = blockIdx.z;
     int n = g.nx;
@@ -638,7 +623,6 @@ __global__ void k_residual(GridDev g, const double *eps, const double2 *E, const
 
 // out[c] = sum_{j,x} |X_j[c][x]|^2 (one block per column, fixed order).
 __global__ void k_colnorm(const double2 *X, int h, int ncol, int nx, double *out) {
-    APF_KERNEL_PROLOGUE();
     __shared__ double red[256];
     int c = blockIdx.x;
     double acc = 0.0;
@@ -659,7 +643,6 @@ __global__ void k_colnorm(const double2 *X, int h, int ncol, int nx, double *out
 // (conj(A) . B, one block per column, fixed order), Y += sgn coef[c] X, and
 // Y = X / sqrt(nrm2[c]) (zero when the norm is zero).
 __global__ void k_coldot(const double2 *A, const double2 *B, int h, int ncol, int nx, double2 *out) {
-    APF_KERNEL_PROLOGUE();
     __shared__ double2 red[256];
     const int c = blockIdx.x;
     double2 acc = cmk(0.0, 0.0);
@@ -677,7 +660,6 @@ __global__ void k_coldot(const double2 *A, const double2 *B, int h, int ncol, in
 }
 
 __global__ void k_colaxpy(double2 *Y, const double2 *X, const double2 *coef, double sgn, int ncol, int nx) {
-    APF_KERNEL_PROLOGUE();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y, j = blockIdx.z;
     if (x >= nx) return;
     const long long i = ((long long)j * ncol + c) * nx + x;
@@ -685,7 +667,6 @@ __global__ void k_colaxpy(double2 *Y, const double2 *X, const double2 *coef, dou
 }
 
 __global__ void k_colscale(double2 *Y, const double2 *X, const double *nrm2, int ncol, int nx) {
-    APF_KERNEL_PROLOGUE();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y, j = blockIdx.z;
     if (x >= nx) return;
     const long long i = ((long long)j * ncol + c) * nx + x;
@@ -694,7 +675,6 @@ __global__ void k_colscale(double2 *Y, const double2 *X, const double *nrm2, int
 }
 
 __global__ void k_axpy(double2 *E, const double2 *d, long long n) {
-    APF_KERNEL_PROLOGUE();
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) E[i] = cadd(E[i], d[i]);
 }
@@ -705,7 +685,6 @@ __global__ void k_axpy(double2 *E, const double2 *d, long long n) {
 __global__ void __launch_bounds__(256) k_grad_rowdot32(const __grid_constant__ Tab<const double2 *> Et, const __grid_constant__ Tab<const float *> Qret,
                                                        const __grid_constant__ Tab<const float *> Qimt, int j, int nx, int n_in, int n_out,
                                                        double k2, const __grid_constant__ Tab<double *> gt) {
-    APF_KERNEL_PROLOGUE();
     __shared__ double part[8][32];
     const double2 *E = Et.v[blockIdx.z];
     const float *Qre = Qret.v[blockIdx.z], *Qim = Qimt.v[blockIdx.z];

@@ -10,7 +10,6 @@ __device__ __forceinline__ int mod_n(int m, int n) { int r = m % n; return r < 0
 // on the last slab row (the projection C_b carried through the cladding).
 __global__ void k_gather_S(const double2 *fft, const double2 *coef, const int *m_out, int n_in, int n_out,
                            int nx, double2 *S) {
-    APF_KERNEL_PROLOGUE();
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     int b = blockIdx.y;
     if (a >= n_in) return;
@@ -29,7 +28,6 @@ struct Orders {
 // (Eq. 5 and the derivative printed after it).  f is reduced in a fixed order.
 __global__ void k_objective(const double2 *S, const int *m_in, const int *m_out, int n_in, int n_out,
                             Orders ord, int kind, double t, double2 *Gam, double *f_out) {
-    APF_KERNEL_PROLOGUE();
     __shared__ double red[1024];
     double acc = 0.0;
     int total = n_in * ord.n;
@@ -70,7 +68,6 @@ __global__ void k_objective(const double2 *S, const int *m_in, const int *m_out,
 // and (C A^-1)_{b,k} = (A^-1 C^T)_{k,b} = Phi_{k,b} because A = A^T.
 __global__ void k_grad_rowdot(const double2 *E, const double2 *Q, int h, int nx, int n_in, int n_out,
                               double k2, double *g) {
-    APF_KERNEL_PROLOGUE();
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (x >= nx) return;
@@ -90,7 +87,6 @@ __global__ void k_grad_rowdot(const double2 *E, const double2 *Q, int h, int nx,
 // lam_a = A^-1 (C_a^adj)^T, C_a^adj = sum_b Gamma_ba C_b, both [row][a][x]
 // with n_in columns.  One thread per pixel, the sum over a in a fixed order.
 __global__ void k_grad_adjoint(const double2 *F, const double2 *Lam, int h, int nx, int n_in, double k2, double *g) {
-    APF_KERNEL_PROLOGUE();
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (x >= nx) return;

@@ -13,7 +13,6 @@ namespace {
 // same value on every slab row.
 __global__ void k_ridge_eps(const double *__restrict__ e, int ne, int mirror, double eps_r, double eps_b, int nx,
                             int h, double *__restrict__ eps) {
-    APF_KERNEL_PROLOGUE();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= nx) return;
     const double lo = (double)x - 0.5 * nx, hi = lo + 1.0;
@@ -32,7 +31,6 @@ __device__ __forceinline__ int wrap(long long p, int nx) { return (int)(((p % nx
 // times -+(eps_r - eps_b).
 __global__ void k_ridge_grad(const double *__restrict__ e, int ne, int mirror, double d_eps, int nx, int h,
                              const double *__restrict__ g, double *__restrict__ out) {
-    APF_KERNEL_PROLOGUE();
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (k >= ne) return;
     const double t = e[k];

@@ -18,7 +18,6 @@ namespace {
 
 __global__ void k_assemble64(GridDev g, int row, const double *eps, const double2 *circ,
                              const double2 *Gprev, double2 *X) {
-    APF_KERNEL_PROLOGUE();
     int xp = blockIdx.x * blockDim.x + threadIdx.x;
     int x = blockIdx.y;
     int n = g.nx;
@@ -42,7 +41,6 @@ __global__ void __launch_bounds__(256) k_zgemm(int M, int N, int K, double2 alph
                                               const double2 *__restrict__ A, long long lda, long long sA,
                                               const double2 *__restrict__ B, long long ldb, long long sB,
                                               double2 beta, double2 *C, long long ldc, long long sC) {
-    APF_KERNEL_PROLOGUE();
     constexpr int BM = 64, BN = 64, BK = 8;
     __shared__ double2 As[BK][BM];
     __shared__ double2 Bs[BK][BN];
@@ -115,7 +113,6 @@ __global__ void __launch_bounds__(256) k_zgemm(int M, int N, int K, double2 alph
 // with partial (row) pivoting, in shared memory.  Row interchanges during the
 // sweep become column interchanges of the result, undone in reverse order.
 __global__ void __launch_bounds__(256) k_leaf_inv64(double2 *X, int n, long long ld, int *flags) {
-    APF_KERNEL_PROLOGUE();
     extern __shared__ double2 a[];  // n*n
     __shared__ double2 colk[64];
     __shared__ int piv[64];
@@ -186,14 +183,12 @@ __global__ void __launch_bounds__(256) k_leaf_inv64(double2 *X, int n, long long
 
 template <int NB>
 __global__ void __launch_bounds__(NB * 4) k_leaf64(double2 *X, long long ld, int *flags) {
-    APF_KERNEL_PROLOGUE();
     LeafIO<double, false> io{nullptr, nullptr, X, ld};
     leaf_gj<double, NB, false>(io, flags);
 }
 
 // C block <- -V, B block <- -V^T  (the off-diagonal blocks of the inverse).
 __global__ void k_neg_offdiag(double2 *Bblk, double2 *Cblk, long long ld, const double2 *V, int h) {
-    APF_KERNEL_PROLOGUE();
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     if (j >= h) return;
@@ -203,13 +198,11 @@ __global__ void k_neg_offdiag(double2 *Bblk, double2 *Cblk, long long ld, const 
 }
 
 __global__ void k_add2(double2 *T, const double2 *a, const double2 *b, long long n) {
-    APF_KERNEL_PROLOGUE();
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) T[i] = cadd(a[i], b[i]);
 }
 
 __global__ void k_copy(double2 *d, const double2 *s, long long n) {
-    APF_KERNEL_PROLOGUE();
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) d[i] = s[i];
 }

@@ -223,9 +223,6 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm(const __grid_constant__ TcAr
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
     int issued = 0;
-    // set-up done; global memory only after the preceding kernel has completed
-    pdl_wait();
-    pdl_launch_dependents();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -445,9 +442,6 @@ __global__ void __launch_bounds__(192, 1) k_tc_gemm_pair(const __grid_constant__
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
     int issued = 0;
-    // set-up done; global memory only after the preceding kernel has completed
-    pdl_wait();
-    pdl_launch_dependents();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -662,18 +656,13 @@ cudaError_t launch_args(apf_ctx *c, K kern, bool pair, unsigned grid, int smem, 
     cfg.blockDim = dim3(192);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[2];
+    cudaLaunchAttribute attr[1];
     int na = 0;
     if (pair) {
         attr[na].id = cudaLaunchAttributeClusterDimension;
         attr[na].val.clusterDim.x = 2;
         attr[na].val.clusterDim.y = 1;
         attr[na].val.clusterDim.z = 1;
-        ++na;
-    }
-    if (pdl_enabled()) {
-        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[na].val.programmaticStreamSerializationAllowed = 1;
         ++na;
     }
     cfg.attrs = attr;

@@ -87,28 +87,3 @@ def test_headers_compile_as_plain_c():
                             src], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
 
-
-def test_every_kernel_waits_for_its_predecessor():
-    """Library kernels are launched with programmatic dependent launch, so
-    each must wait for the preceding grid (griddepcontrol.wait) before it
-    touches global memory: every __global__ function in csrc/ (the surrogate
-    kernels are launched without the attribute) starts with
-    APF_KERNEL_PROLOGUE, or calls pdl_wait in its body (the GEMM kernels,
-    after their barrier and tensor-memory set-up)."""
-    csrc = os.path.join(ROOT, "paper_2306_09257_gb300", "csrc")
-    missing = []
-    for f in sorted(os.listdir(csrc)):
-        if not f.endswith(".cu") or f == "surrogate.cu":
-            continue
-        src = open(os.path.join(csrc, f)).read()
-        for m in re.finditer(r"__global__\s+void[^;{]*?\)\s*\{", src, re.S):
-            # the kernel body: up to the matching closing brace
-            depth, i = 1, m.end()
-            while depth and i < len(src):
-                depth += {"{": 1, "}": -1}.get(src[i], 0)
-                i += 1
-            body = src[m.end():i]
-            name = re.search(r"(k_\w+)\s*\(", m.group(0))
-            if "APF_KERNEL_PROLOGUE" not in body[:200] and "pdl_wait()" not in body:
-                missing.append(f"{f}:{name.group(1) if name else '?'}")
-    assert not missing, missing
