@@ -170,6 +170,7 @@ int apf_create(apf_ctx **out, int cuda_device, int precision) {
     c->device = cuda_device;
     c->precision = precision;
     c->butterfly = precision == APF_MIXED_BF16X3 ? 1 : 0;  // see apf_set_elimination
+    if (const char *e = getenv("APF_GRAPHS")) c->use_graphs = e[0] != '0';  // diagnostic knob: 0 = launch eagerly
     for (auto &ev : c->ev) cudaEventCreate(&ev);
     cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     slab64_init_attrs();
