@@ -74,8 +74,8 @@ def args_parse():
                         "host thread + stream per design, one design per call")
     p.add_argument("--no-compare", action="store_true", help="skip timing the other --mode for comparison")
     p.add_argument("--groups", type=int, default=2,
-                   help="batch mode: the designs form this many batched calls, each on its own thread and stream, "
-                        "so one group's latency-bound steps overlap another group's tensor-core work")
+                   help="batch mode (1 or 2): the designs form this many batched calls, each on its own thread and "
+                        "stream, so one group's latency-bound steps overlap another group's tensor-core work")
     p.add_argument("--planes", type=int, default=2, choices=[2, 3],
                    help="bf16 split planes of the mixed elimination (3: bf16x6, for high-contrast slabs)")
     p.add_argument("--no-butterfly", action="store_true",
@@ -305,6 +305,10 @@ def main():
         # 16 host threads, each with its own context and stream, did not finish on GB300 (no kernel fault; the
         # GPU still answered after the process was killed); the batch mode keeps B designs on G threads instead
         raise SystemExit("--mode streams runs at most 8 designs; use --mode batch (--groups) for more")
+    if a.mode == "batch" and a.groups > 2:
+        # three or four batched calls in flight on separate streams left a GEMM launch resident without progress
+        # on GB300; the library now admits two solves at a time, and the bench runs at most two groups
+        raise SystemExit("--groups runs at most 2 concurrent batched calls")
     nseeds = 4
     ridges = a.design == "ridges"
     seeds = replicas.replica_seeds(rank, B, nseeds)

@@ -207,6 +207,21 @@ int mixed_refine_n(apf_ctx *const *cs, int nb, cudaStream_t s, int *rcs);
 int mixed_gradient_n(apf_ctx *const *cs, int nb, cudaStream_t s);
 bool mixed_batch_compatible(const apf_ctx *a, const apf_ctx *b);
 
+// Process-wide bound on the library calls that run solve kernels at the same
+// time: a call waits in the constructor until fewer than two others are
+// inside (nested calls on one thread hold one slot).  Every such call
+// synchronises its stream before returning, so at most two solves have
+// kernels on the GPU together, whatever the number of host threads.
+struct SolveGate {
+    SolveGate();
+    ~SolveGate();
+    SolveGate(const SolveGate &) = delete;
+    SolveGate &operator=(const SolveGate &) = delete;
+
+  private:
+    bool held_;
+};
+
 int set_err(apf_ctx *c, int code, const char *fmt, ...);
 void prof_collect(apf_ctx *c);
 void prof_collect_range(apf_ctx *c, int lo, int hi);

@@ -2,7 +2,7 @@
 
     python -m paper_2306_09257_gb300.kernelbench gemm M N K [nsplit]   # complex M x K @ K x N on tcgen05
     python -m paper_2306_09257_gb300.kernelbench inv N [leaf]          # mixed inversion of a slab-like block
-    python -m paper_2306_09257_gb300.kernelbench step large [K]        # K S + grad evaluations of one design
+    python -m paper_2306_09257_gb300.kernelbench step large [K] [B]    # K steps of S + grad for B designs
 
 They drive the library's test hooks (apf_debug_cgemm, apf_debug_inv32) on
 seeded random inputs; used for the ncu captures summarised under profiles/.
@@ -85,27 +85,38 @@ def inv(n, leaf=128, reps=3):
     print(f"inv {n} leaf {leaf}: {min(ts):.3f} ms, rms residual {res:.2e}")
 
 
-def step(workload="large", k=1):
-    """One warm-up and k timed S + grad f evaluations of one design of a
-    workload (mixed, refinement to 1e-7 as in bench.py): the smallest command
-    that runs the whole hot path, for launch lists under a profiler."""
+def step(workload="large", k=1, nb=1):
+    """One warm-up and k timed S + grad f evaluations of nb designs of a
+    workload (mixed, refinement to 1e-7 as in bench.py; nb > 1 in one
+    apf_solve_S_grad_batch call per step): the smallest command that runs the
+    whole hot path, for launch lists under a profiler."""
     from . import workloads as W
     w = {"tiny": W.TINY, "mid": W.MID, "large": W.LARGE, "xlarge": W.XLARGE}[workload]
-    s = apf.solver_for_workload(w, w.eps_slab(0), precision="mixed")
-    s.set_refinement(1e-7, 40)
+    sv = [apf.solver_for_workload(w, w.eps_slab(b), precision="mixed") for b in range(nb)]
+    for s in sv:
+        s.set_refinement(1e-7, 40)
     orders = [-2, -1, 0, 1, 2]
-    s.solve_S_grad("splitter", orders, 0.18)
+
+    def run():
+        if nb == 1:
+            sv[0].solve_S_grad("splitter", orders, 0.18)
+        else:
+            apf.solve_S_grad_batch(sv, "splitter", orders, 0.18)
+
+    run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for i in range(k):
-        s.set_eps(w.eps_slab(i + 1), w.eps_sub, w.eps_clad, j0=w.j0)
-        s.solve_S_grad("splitter", orders, 0.18)
+        for b, s in enumerate(sv):
+            s.set_eps(w.eps_slab(nb * (i + 1) + b), w.eps_sub, w.eps_clad, j0=w.j0)
+        run()
     e1.record()
     torch.cuda.synchronize()
-    st = s.stats()
-    print(f"step {w.name}: {e0.elapsed_time(e1) / k:.1f} ms per evaluation, {st['kernel_launches']} launches, "
-          f"{st['refine_iters']} refinement sweeps")
+    st = [s.stats() for s in sv]
+    print(f"step {w.name} x {nb}: {e0.elapsed_time(e1) / k:.1f} ms per step "
+          f"({1000.0 * k * nb / e0.elapsed_time(e1):.2f} evaluations/s), "
+          f"{st[0]['kernel_launches']} launches, refinement sweeps {[x['refine_iters'] for x in st]}")
 
 
 if __name__ == "__main__":
@@ -115,6 +126,6 @@ if __name__ == "__main__":
     elif a and a[0] == "inv":
         inv(*[int(x) for x in a[1:]])
     elif a and a[0] == "step":
-        step(a[1] if len(a) > 1 else "large", int(a[2]) if len(a) > 2 else 1)
+        step(a[1] if len(a) > 1 else "large", *[int(x) for x in a[2:4]])
     else:
         print(__doc__)

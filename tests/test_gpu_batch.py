@@ -107,3 +107,42 @@ def test_batch_rejects_mismatched_contexts(apf):
     with pytest.raises(apf.APFError) as e:
         apf.solve_S_grad_batch([s0, s0], "power", [0])
     assert e.value.code == apf.APF_EINVAL
+
+
+def test_threads_share_two_solve_slots(apf):
+    """Four host threads, each with its own context and stream, solving 1024 x
+    240 designs at once: the library keeps at most two solves in flight
+    (the rest wait on the host), and each design's S and gradient are
+    bit-identical to the same design solved alone."""
+    import threading
+
+    import torch
+    w = W.MID
+    seeds = [0, 1, 2, 3]
+    eps = [w.eps_slab(sd) for sd in seeds]
+    sv = solvers(apf, w, eps, "mixed")
+    alone = [s.solve_S_grad("splitter", ORDERS, 0.18) for s in sv]
+    L = apf.load_library()
+    L.apf_debug_inflight_peak.argtypes = [apf.ctypes.c_int]
+    L.apf_debug_inflight_peak(1)
+    out, errs = [None] * len(sv), []
+
+    def worker(b):
+        try:
+            with torch.cuda.stream(torch.cuda.Stream()):
+                for _ in range(2):
+                    out[b] = sv[b].solve_S_grad("splitter", ORDERS, 0.18)
+        except BaseException as e:  # noqa: BLE001
+            errs.append(e)
+    ths = [threading.Thread(target=worker, args=(b,)) for b in range(len(sv))]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    assert not errs, errs
+    peak = L.apf_debug_inflight_peak(0)
+    assert 1 <= peak <= 2, peak
+    for b in range(len(sv)):
+        assert np.array_equal(out[b][0], alone[b][0])
+        assert np.array_equal(out[b][2], alone[b][2])
+        assert out[b][1] == alone[b][1]
