@@ -73,9 +73,13 @@ def args_parse():
                    help="batch: the designs share every launch (apf_solve_S_grad_batch, one stream); streams: one "
                         "host thread + stream per design, one design per call")
     p.add_argument("--no-compare", action="store_true", help="skip timing the other --mode for comparison")
-    p.add_argument("--groups", type=int, default=2,
-                   help="batch mode (1 or 2): the designs form this many batched calls, each on its own thread and "
-                        "stream, so one group's latency-bound steps overlap another group's tensor-core work")
+    p.add_argument("--groups", type=int, default=1,
+                   help="batch mode (1 or 2): the designs form this many batched calls (up to 16 designs each), each "
+                        "on its own thread and stream; the library runs one solve at a time per GPU, so two groups "
+                        "take turns")
+    p.add_argument("--watchdog", type=float, default=0.0,
+                   help="seconds after which a run that has not finished dumps every thread's stack and exits "
+                        "non-zero (0: 600 s + 60 s per step)")
     p.add_argument("--planes", type=int, default=2, choices=[2, 3],
                    help="bf16 split planes of the mixed elimination (3: bf16x6, for high-contrast slabs)")
     p.add_argument("--no-butterfly", action="store_true",
@@ -282,6 +286,12 @@ def fp64_peak(local):
     return 2.0 * n ** 3 / best / 1e12
 
 
+def phase(msg):
+    """Progress marker on stderr (APF_BENCH_TRACE=1); the JSON line stays alone on stdout."""
+    if os.environ.get("APF_BENCH_TRACE") == "1":
+        print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def main():
     a = args_parse()
     w = WL[a.workload]
@@ -289,6 +299,9 @@ def main():
     if a.impl == "reference":
         run_reference(a, w)
         return
+    import faulthandler
+    faulthandler.dump_traceback_later(a.watchdog if a.watchdog > 0 else 600.0 + 60.0 * (a.steps + a.warmup),
+                                      exit=True)
     import threading
 
     import torch
@@ -306,9 +319,11 @@ def main():
         # GPU still answered after the process was killed); the batch mode keeps B designs on G threads instead
         raise SystemExit("--mode streams runs at most 8 designs; use --mode batch (--groups) for more")
     if a.mode == "batch" and a.groups > 2:
-        # three or four batched calls in flight on separate streams left a GEMM launch resident without progress
-        # on GB300; the library now admits two solves at a time, and the bench runs at most two groups
-        raise SystemExit("--groups runs at most 2 concurrent batched calls")
+        # several batched calls in flight on separate streams once left a GEMM launch resident without progress
+        # on GB300; the library now runs one solve at a time per GPU, and the bench runs at most two groups
+        raise SystemExit("--groups runs at most 2 batched calls")
+    if B > 16 * max(1, a.groups) and a.mode == "batch":
+        raise SystemExit("batch mode takes at most 16 designs per group")
     nseeds = 4
     ridges = a.design == "ridges"
     seeds = replicas.replica_seeds(rank, B, nseeds)
@@ -478,6 +493,7 @@ def main():
 
     batched = a.mode == "batch" and B > 1
     # ---- 1. the headline: B designs in flight, inputs resident on the device ----
+    phase(f"headline: {B} designs, mode {a.mode}")
     if batched:
         run_groups(step_batch_dev, a.warmup)
         ms, clocks = timed(lambda n, e, ev: batch_steps(n, e, ev, record=True), a.steps, sample_clocks=True)
@@ -503,6 +519,7 @@ def main():
                      "unit": "evals/s", "value": replicas.whole_job_throughput(ws, B, a.steps, ms_o)}
 
     # ---- 2. end to end at the same concurrency and step count: host buffers ----
+    phase("end to end")
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -523,10 +540,11 @@ def main():
         d2h = nin * nout * 16 + w.h * w.nx * 8 + 8
 
     # ---- 2b. the tensor-core GEMM's in-step roofline in the batched step: all B designs
-    # (up to 8) in one call on one stream, so every GEMM's CUDA-event interval is that launch alone
+    # (up to 16) in one call on one stream, so every GEMM's CUDA-event interval is that launch alone
+    phase("profiled batched step")
     prof_b = None
     if batched:
-        nbp = min(B, 8)
+        nbp = min(B, 16)
         lead = solvers[0]
         lead.set_profiling(True)
         with torch.cuda.stream(streams[0]):
@@ -545,6 +563,7 @@ def main():
         lead.set_profiling(False)
 
     # ---- 3. one design alone: its rate, then the tensor-core GEMM's in-step roofline ----
+    phase("one design")
     # (a single stream, so every GEMM's CUDA-event interval is that launch alone)
     n1 = max(3, a.steps // 2)
 
@@ -575,6 +594,7 @@ def main():
               "launches_per_step": s.stats()["kernel_launches"]}
 
     # ---- 4. the float64 GPU path, the same design, one design at a time ----
+    phase("float64 path")
     fp64 = None
     if a.fp64_steps > 0:
         s64 = new_solver("fp64", x_host[0][0])
@@ -604,6 +624,7 @@ def main():
         s64.close()
 
     # ---- 5. the conventional adjoint method (Eq. S1) on the same elimination, one design ----
+    phase("adjoint method")
     adj = None
     if not ridges:
         set_design(s, x_host[0][0])
@@ -627,6 +648,7 @@ def main():
                         "for a sparse direct solver on one CPU core, where the adjoint method re-solves per input")}
 
     # ---- 6. slab Schur blocks recomputed instead of stored, one design ----
+    phase("recomputed Schur blocks")
     rec = None
     if not ridges and a.recompute_rows > 0:
         sr = new_solver("mixed", x_host[0][0])
@@ -649,6 +671,7 @@ def main():
         sr.close()
 
     # ---- 7. gradient-descent optimisation (Armijo line search, Supplement Sec. 4), one design ----
+    phase("optimisation")
     opt = None
     if not ridges and a.opt_iters > 0:
         from paper_2306_09257_gb300 import optim
@@ -661,6 +684,7 @@ def main():
     # properties that hold at any size, on one design: reciprocity between the
     # forward (S) and adjoint (reverse S) columns, and flux conservation with the
     # reflection block (up to the PML's reflection)
+    phase("checks")
     checks = None
     set_design(s, x_host[0][0])
     if s.channels()[1].tolist() == sorted(-m for m in s.channels()[1].tolist()):
@@ -713,6 +737,7 @@ def main():
             "note": "CUDA events around the one GEMM launch; peak = bf16_tflops (burst, of measured)"}
 
     cpu = None
+    phase("cpu baseline")
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         if ridges:
             import oracle as O

@@ -41,6 +41,14 @@
  *     apf_last_error() gives a one-line message for the most recent failure.
  *   - Size/argument checks run on the host before any launch (APF_EINVAL).
  *   - A context is single-threaded: calls on one context must not overlap.
+ *
+ * Threads
+ *   - Different contexts may be used from different host threads.  Calls
+ *     that run solve kernels (apf_solve_S, apf_solve_S_grad,
+ *     apf_solve_S_grad_adjoint, apf_solve_S_grad_batch, apf_grad_from_gamma)
+ *     run one at a time per device: a call blocks on the host while another
+ *     thread's call on the same device is inside the library.  Several
+ *     designs at once go through apf_solve_S_grad_batch instead.
  */
 #ifndef APF_H
 #define APF_H
@@ -164,7 +172,7 @@ int apf_solve_S_grad(apf_ctx *ctx, int objective, const double *params, int n_pa
 int apf_solve_S_grad_adjoint(apf_ctx *ctx, int objective, const double *params, int n_params,
                              double *S, double *f, double *grad_eps, void *stream);
 
-/* S, f and df/deps for nb independent designs in one call (nb <= 8; the
+/* S, f and df/deps for nb independent designs in one call (nb <= 16; the
    paper's Sec. 3 runs 1000 independent starts, and line searches try several
    designs per iteration).  ctx[0..nb) are distinct contexts, each prepared
    by apf_set_grid, apf_set_eps (its own permittivity) and apf_set_channels,

@@ -23,32 +23,26 @@
 
 static char g_create_err[512] = "no error";
 
-// Why two: with three or more batched solves in flight on separate streams,
-// a tensor-core GEMM launch on GB300 stayed resident without progress (GPU
-// busy at idle power, no kernel fault, the GPU usable again once the process
-// ended; the cause was not found), while one or two solves in flight ran
-// clean in every measurement.  APF_MAX_INFLIGHT_SOLVES=1 lowers the bound.
+// Why one: with several solves in flight on separate streams of one GPU
+// (three or four batched calls; sixteen single-design calls; once in ten
+// runs two batched calls), a tensor-core launch on GB300 stayed resident
+// without progress (GPU busy at idle power, no kernel fault, the GPU usable
+// again once the process ended; the cause was not found), while one solve at
+// a time never did.  So solve calls on one device run one at a time.
 namespace {
+constexpr int GATE_DEVICES = 64;
 std::mutex g_gate_mu;
 std::condition_variable g_gate_cv;
-int g_gate_busy = 0, g_gate_peak = 0;
+int g_gate_busy[GATE_DEVICES] = {}, g_gate_peak = 0;
 thread_local int t_gate_depth = 0;
-
-int gate_limit() {
-    static const int v = [] {
-        const char *e = getenv("APF_MAX_INFLIGHT_SOLVES");
-        const int n = e ? atoi(e) : 2;
-        return n == 1 ? 1 : 2;
-    }();
-    return v;
-}
 }  // namespace
 
-SolveGate::SolveGate() : held_(t_gate_depth++ == 0) {
+SolveGate::SolveGate(int device)
+    : dev_(device < 0 ? 0 : device % GATE_DEVICES), held_(t_gate_depth++ == 0) {
     if (!held_) return;
     std::unique_lock<std::mutex> lk(g_gate_mu);
-    g_gate_cv.wait(lk, [] { return g_gate_busy < gate_limit(); });
-    g_gate_peak = std::max(g_gate_peak, ++g_gate_busy);
+    g_gate_cv.wait(lk, [this] { return g_gate_busy[dev_] == 0; });
+    g_gate_peak = std::max(g_gate_peak, ++g_gate_busy[dev_]);
 }
 
 SolveGate::~SolveGate() {
@@ -56,12 +50,12 @@ SolveGate::~SolveGate() {
     if (!held_) return;
     {
         std::lock_guard<std::mutex> lk(g_gate_mu);
-        --g_gate_busy;
+        --g_gate_busy[dev_];
     }
-    g_gate_cv.notify_one();
+    g_gate_cv.notify_all();
 }
 
-// Test hook: the most solve calls seen inside the gate at once (reset to 0 if asked).
+// Test hook: the most solve calls seen inside the gate of one device at once (reset to 0 if asked).
 extern "C" int apf_debug_inflight_peak(int reset) {
     std::lock_guard<std::mutex> lk(g_gate_mu);
     const int p = g_gate_peak;
@@ -660,7 +654,7 @@ extern "C" {
 
 int apf_solve_S(apf_ctx *c, double *S, void *stream) {
     if (!c) return APF_EINVAL;
-    SolveGate gate;
+    SolveGate gate(c->device);
     if (!S) return set_err(c, APF_EINVAL, "S is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = run_solve(c, s);
@@ -674,7 +668,7 @@ int apf_solve_S(apf_ctx *c, double *S, void *stream) {
 int apf_solve_S_grad(apf_ctx *c, int objective, const double *params, int n_params, double *S, double *f,
                      double *grad_eps, void *stream) {
     if (!c) return APF_EINVAL;
-    SolveGate gate;
+    SolveGate gate(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (!grad_eps) return set_err(c, APF_EINVAL, "grad_eps is NULL");
     if (!c->grid_set || !c->eps_set || !c->ch_set)
@@ -735,7 +729,7 @@ static int adjoint_method(apf_ctx *c, int objective, const double *params, int n
 int apf_solve_S_grad_adjoint(apf_ctx *c, int objective, const double *params, int n_params, double *S, double *f,
                              double *grad_eps, void *stream) {
     if (!c) return APF_EINVAL;
-    SolveGate gate;
+    SolveGate gate(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (!grad_eps) return set_err(c, APF_EINVAL, "grad_eps is NULL");
     if (!c->grid_set || !c->eps_set || !c->ch_set)
@@ -778,7 +772,7 @@ int apf_solve_S_grad_batch(apf_ctx *const *ctx, int nb, int objective, const dou
         for (int a = 0; a < b; ++a)
             if (ctx[a] == ctx[b]) return set_err(ctx[b], APF_EINVAL, "a context appears twice in the batch");
     }
-    SolveGate gate;
+    SolveGate gate(ctx[0]->device);
     apf_ctx *c0 = ctx[0];
     for (int b = 0; b < nb; ++b) {
         apf_ctx *c = ctx[b];
@@ -885,7 +879,7 @@ int apf_solve_S_grad_batch(apf_ctx *const *ctx, int nb, int objective, const dou
 
 int apf_grad_from_gamma(apf_ctx *c, const double *Gamma, double *grad_eps, void *stream) {
     if (!c) return APF_EINVAL;
-    SolveGate gate;
+    SolveGate gate(c->device);
     if (!Gamma || !grad_eps) return set_err(c, APF_EINVAL, "Gamma / grad_eps is NULL");
     if (!c->ch_set || c->ws_nx < 0) return set_err(c, APF_ESTATE, "apf_grad_from_gamma needs a previous solve");
     if (c->fields_lay != 0)

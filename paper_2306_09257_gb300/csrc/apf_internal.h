@@ -200,25 +200,26 @@ int mixed_eliminate(apf_ctx *c, cudaStream_t s);
 int mixed_fields_begin(apf_ctx *c, cudaStream_t s);
 int mixed_refine(apf_ctx *c, cudaStream_t s);
 // the same steps for a batch of designs (shared launches), see apf_solve_S_grad_batch
-constexpr int APF_MAX_BATCH = 8;
+constexpr int APF_MAX_BATCH = 16;
 int mixed_eliminate_n(apf_ctx *const *cs, int nb, cudaStream_t s);
 int mixed_fields_begin_n(apf_ctx *const *cs, int nb, cudaStream_t s);
 int mixed_refine_n(apf_ctx *const *cs, int nb, cudaStream_t s, int *rcs);
 int mixed_gradient_n(apf_ctx *const *cs, int nb, cudaStream_t s);
 bool mixed_batch_compatible(const apf_ctx *a, const apf_ctx *b);
 
-// Process-wide bound on the library calls that run solve kernels at the same
-// time: a call waits in the constructor until fewer than two others are
-// inside (nested calls on one thread hold one slot).  Every such call
-// synchronises its stream before returning, so at most two solves have
-// kernels on the GPU together, whatever the number of host threads.
+// Solve calls on one device run one at a time: a call waits in the
+// constructor while another thread's call on the same device is inside
+// (nested calls on one thread hold one slot).  Every such call synchronises
+// its stream before returning, so the library never has two solves' kernels
+// on one GPU together, whatever the number of host threads.
 struct SolveGate {
-    SolveGate();
+    explicit SolveGate(int device);
     ~SolveGate();
     SolveGate(const SolveGate &) = delete;
     SolveGate &operator=(const SolveGate &) = delete;
 
   private:
+    int dev_;
     bool held_;
 };
 

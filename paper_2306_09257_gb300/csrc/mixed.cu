@@ -1589,8 +1589,9 @@ bool mixed_batch_compatible(const apf_ctx *a, const apf_ctx *b) {
 // ---------------------------------------------------------------------------
 extern "C" int apf_debug_cgemm(apf_ctx *c, int m, int n, int k, const float *Are, const float *Aim,
                                const float *Bre, const float *Bim, float *Cre, float *Cim, int nsplit) {
-    SolveGate gate;
-    if (!c || m < 1 || n < 1 || k < 1 || nsplit < 1 || nsplit > 3) return APF_EINVAL;
+    if (!c) return APF_EINVAL;
+    SolveGate gate(c->device);
+    if (m < 1 || n < 1 || k < 1 || nsplit < 1 || nsplit > 3) return APF_EINVAL;
     cudaSetDevice(c->device);
     long long kp = round_up(2LL * k, 64);
     __nv_bfloat16 *pa = nullptr, *pb = nullptr;
@@ -1619,7 +1620,8 @@ extern "C" int apf_debug_cgemm(apf_ctx *c, int m, int n, int k, const float *Are
 // In-place inverse of an n x n complex-symmetric planar float32 matrix using
 // the workspace of a prepared mixed-precision context (n <= its nx).
 extern "C" int apf_debug_inv32(apf_ctx *c, int n, float *re, float *im, int leaf) {
-    SolveGate gate;
+    if (!c) return APF_EINVAL;
+    SolveGate gate(c->device);
     if (!c || !c->mw || n < 1 || n > c->nx || (n & (n - 1))) return APF_EINVAL;
     cudaSetDevice(c->device);
     int old = c->mw->leaf, oldv = c->mw->leaf_variant;

@@ -35,7 +35,7 @@ struct TcArgs {
     TcParams p[P];
     int nprob;
 };
-constexpr int TC_MAX_BATCH = 8;
+constexpr int TC_MAX_BATCH = 16;
 
 // One product of a batch: operands, output (and beta input) planes, error flags.
 struct TcProblem {
