@@ -45,10 +45,10 @@
  * Threads
  *   - Different contexts may be used from different host threads.  Calls
  *     that run solve kernels (apf_solve_S, apf_solve_S_grad,
- *     apf_solve_S_grad_adjoint, apf_solve_S_grad_batch, apf_grad_from_gamma)
- *     run one at a time per device: a call blocks on the host while another
- *     thread's call on the same device is inside the library.  Several
- *     designs at once go through apf_solve_S_grad_batch instead.
+ *     apf_solve_S_grad_adjoint, apf_solve_S_grad_batch, apf_grad_from_gamma,
+ *     apf_solve_S_noalloc) run one at a time per device: a call blocks on
+ *     the host while another thread's call on the same device is inside the
+ *     library.  Several designs at once go through apf_solve_S_grad_batch.
  */
 #ifndef APF_H
 #define APF_H
@@ -349,8 +349,9 @@ int apf_get_profile(const apf_ctx *ctx, apf_profile *prof);
    before any stream capture.  The call runs on the current device, enqueues
    on `stream` and synchronizes it before returning.  Every call shares the
    one array and leaves its contents behind (each call zeroes what must start
-   at zero), so calls whose GPU work overlaps -- from two host threads or two
-   streams at once -- race on it and must be serialized by the caller. */
+   at zero); calls on one device take turns like every solve of the library
+   (a call blocks on the host while another is inside, see Threads above),
+   so calls from several host threads or streams never overlap on it. */
 #define APF_NOALLOC_SCRATCH_BYTES (4u << 20)
 int apf_solve_S_noalloc(int nx, int ny, int npml_bot, int npml_top, double lambda_px,
                         const apf_pml_params *pml, const double *eps_slab, int j0, int h,

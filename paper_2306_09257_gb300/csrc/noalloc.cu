@@ -97,6 +97,9 @@ extern "C" int apf_solve_S_noalloc(int nx, int ny, int npml_bot, int npml_top, d
         cudaGetLastError();
         return fail(APF_ECUDA, "no current CUDA device");
     }
+    // one call at a time per device (with every other solve of the library),
+    // so overlapping calls from several threads never share the scratch array
+    SolveGate gate(dev);
     if (!g_scratch_dev[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);

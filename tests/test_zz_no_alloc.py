@@ -121,3 +121,44 @@ def test_noalloc_rejects_just_over_the_limit(lib, what):
                                orders, n, orders, n, out.ctypes.data, None)
     assert rc == apf.APF_EINVAL
     assert (b"h must be" if what == "h" else b"channels") in L.apf_last_error(None)
+
+
+def test_noalloc_threads_take_turns(lib):
+    """Four host threads call the allocation-free solve at once, each with its
+    own design and stream: calls on one device take turns, so none sees
+    another's data in the shared scratch array (each S equals its own
+    context-based solve)."""
+    import threading
+
+    import torch
+    apf, L = lib
+    w = W.TINY
+    seeds = [3, 4, 5, 6]
+    eps = [np.ascontiguousarray(w.eps_slab(sd)) for sd in seeds]
+    refs = []
+    for e in eps:
+        s = apf.solver_for_workload(w, e, precision="fp64")
+        refs.append(s.solve_S())
+        s.close()
+    outs = [np.full(r.shape, np.nan + 1j * np.nan) for r in refs]
+    errs = []
+
+    def worker(b):
+        try:
+            st = torch.cuda.Stream()
+            for _ in range(3):
+                rc = L.apf_solve_S_noalloc(w.nx, w.ny, w.npml, w.npml, w.lambda_px, None, eps[b].ctypes.data,
+                                           w.j0, w.h, w.eps_sub, w.eps_clad, None, 0, None, 0,
+                                           outs[b].ctypes.data, ctypes.c_void_p(st.cuda_stream))
+                assert rc == 0, L.apf_last_error(None)
+        except BaseException as e:  # noqa: BLE001
+            errs.append(e)
+    ths = [threading.Thread(target=worker, args=(b,)) for b in range(len(seeds))]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    assert not errs, errs
+    for b in range(len(seeds)):
+        err = np.linalg.norm(outs[b] - refs[b]) / np.linalg.norm(refs[b])
+        assert err <= TOL_FP64, (seeds[b], err)
