@@ -77,6 +77,9 @@ def args_parse():
                    help="batch mode (1 or 2): the designs form this many batched calls (up to 16 designs each), each "
                         "on its own thread and stream; the library runs one solve at a time per GPU, so two groups "
                         "take turns")
+    p.add_argument("--schur-segment", type=int, default=0,
+                   help="headline designs: keep one segment of this many slab rows of inverses and recompute the "
+                        "others from checkpoints (0: store every inverse); lets more designs fit in HBM")
     p.add_argument("--watchdog", type=float, default=0.0,
                    help="seconds after which a run that has not finished dumps every thread's stack and exits "
                         "non-zero (0: 600 s + 60 s per step)")
@@ -341,10 +344,12 @@ def main():
         else:
             sv.set_eps(x, w.eps_sub, w.eps_clad, j0=w.j0)
 
-    def new_solver(prec, x):
+    def new_solver(prec, x, seg=0):
         sv = apf.Solver(device=local, precision=prec)
         sv.set_grid(w.nx, w.ny, w.npml, w.npml, w.lambda_px)
         set_design(sv, x)
+        if seg > 0:
+            sv.set_schur_storage(seg)  # before the workspace exists: no full-size allocation first
         sv.set_channels(None, None)
         if prec == "mixed":
             sv.set_refinement(a.refine_tol, 40)
@@ -352,7 +357,7 @@ def main():
                 sv.set_elimination(a.planes, not a.no_butterfly)
         return sv
 
-    solvers = [new_solver("mixed", x_host[b][0]) for b in range(B)]
+    solvers = [new_solver("mixed", x_host[b][0], a.schur_segment) for b in range(B)]
     s = solvers[0]
     m_in, m_out = s.channels()
     nin, nout = len(m_in), len(m_out)
@@ -763,7 +768,7 @@ def main():
                            "refine_iters": iters, "residual": st_last["residual"],
                            "leaf_fallbacks_per_step": sum(x["fallbacks"] for x in stats_acc) / (B * a.steps),
                            "concurrent_designs_per_gpu": B, "elimination_planes": a.planes,
-                           "butterfly": not a.no_butterfly,
+                           "butterfly": not a.no_butterfly, "schur_segment_rows": a.schur_segment,
                            "mode": (f"apf_solve_S_grad_batch: {G} group(s) of {len(groups[0])} designs, each group "
                                     f"sharing every launch, one thread + stream per group" if batched else
                                     "one host thread + stream per design"),

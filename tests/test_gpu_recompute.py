@@ -80,3 +80,33 @@ def test_schur_storage_arguments(apf):
     m = apf.Solver(0, "mixed")
     with pytest.raises(apf.APFError):
         m.set_schur_storage(-1)
+
+
+def test_batch_recompute_is_bit_identical(apf):
+    """Three 1024 x 240 designs in one batched call: recomputing the slab
+    inverses in segments of 5 rows (ragged last segment, h = 12) gives the
+    same bits as storing them, design by design."""
+    w = W.MID
+    eps = [w.eps_slab(sd) for sd in (3, 4, 5)]
+
+    def batch(seg):
+        sv = []
+        for e in eps:
+            s = apf.Solver(0, "mixed")
+            s.set_grid(w.nx, w.ny, w.npml, w.npml, w.lambda_px)
+            s.set_eps(e, w.eps_sub, w.eps_clad, j0=w.j0)
+            s.set_schur_storage(seg)
+            s.set_channels(None, None)
+            s.set_refinement(1e-10, 40)
+            sv.append(s)
+        out = apf.solve_S_grad_batch(sv, "splitter", ORDERS, 0.18)
+        ws = [s.stats()["workspace_bytes"] for s in sv]
+        for s in sv:
+            s.close()
+        return out, ws
+
+    (Sa, fa, ga), wa = batch(0)
+    (Sb, fb, gb), wb = batch(5)
+    for d in range(len(eps)):
+        assert np.array_equal(Sa[d], Sb[d]) and fa[d] == fb[d] and np.array_equal(ga[d], gb[d])
+        assert wb[d] < wa[d]
