@@ -302,6 +302,17 @@ def main():
     if a.impl == "reference":
         run_reference(a, w)
         return
+    B = max(1, a.concurrent)
+    if a.mode == "streams" and B > 8:
+        # 16 host threads, each with its own context and stream, did not finish on GB300 (no kernel fault; the
+        # GPU still answered after the process was killed); the batch mode keeps B designs on G threads instead
+        raise SystemExit("--mode streams runs at most 8 designs; use --mode batch (--groups) for more")
+    if a.mode == "batch" and a.groups > 2:
+        # several batched calls in flight on separate streams once left a GEMM launch resident without progress
+        # on GB300; the library now runs one solve at a time per GPU, and the bench runs at most two groups
+        raise SystemExit("--groups runs at most 2 batched calls")
+    if B > 16 * max(1, a.groups) and a.mode == "batch":
+        raise SystemExit("batch mode takes at most 16 designs per group")
     import faulthandler
     faulthandler.dump_traceback_later(a.watchdog if a.watchdog > 0 else 600.0 + 60.0 * (a.steps + a.warmup),
                                       exit=True)
@@ -316,17 +327,6 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    B = max(1, a.concurrent)
-    if a.mode == "streams" and B > 8:
-        # 16 host threads, each with its own context and stream, did not finish on GB300 (no kernel fault; the
-        # GPU still answered after the process was killed); the batch mode keeps B designs on G threads instead
-        raise SystemExit("--mode streams runs at most 8 designs; use --mode batch (--groups) for more")
-    if a.mode == "batch" and a.groups > 2:
-        # several batched calls in flight on separate streams once left a GEMM launch resident without progress
-        # on GB300; the library now runs one solve at a time per GPU, and the bench runs at most two groups
-        raise SystemExit("--groups runs at most 2 batched calls")
-    if B > 16 * max(1, a.groups) and a.mode == "batch":
-        raise SystemExit("batch mode takes at most 16 designs per group")
     nseeds = 4
     ridges = a.design == "ridges"
     seeds = replicas.replica_seeds(rank, B, nseeds)
