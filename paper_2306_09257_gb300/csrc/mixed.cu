@@ -600,37 +600,59 @@ __global__ void k_circ_apply(const double2 *in, double2 *out, int n, int logn, c
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = cscale(a[i], s);
 }
 
-// r_j = R_j - K E restricted to the slab, float64.
+// r_j = R_j - K E restricted to the slab, float64.  K E at a pixel is
+// d E - (sum of the four neighbours) + boundary terms, d = 4 - k^2 eps; the
+// neighbour sum and the boundary terms are gathered first so that the
+// diagonal term is one fused multiply-add per component.
 __global__ void k_residual(GridDev g, const double *eps, const double2 *E, const double2 *R, const double2 *cb,
                            const double2 *ct, double2 *r, int ncol) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int c = blockIdx.y, j = blockIdx.z;
-    int n = g.nx;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y, j = blockIdx.z;
+    const int n = g.nx;
     if (x >= n) return;
-    long long L = (long long)ncol * n;
+    const long long L = (long long)ncol * n;
     const double2 *e = E + j * L + (long long)c * n;
-    double d = 4.0 - g.k * g.k * eps[(long long)j * n + x];
-    double2 v = cscale(e[x], d);
-    v = csub(v, e[(x + 1) % n]);
-    v = csub(v, e[(x + n - 1) % n]);
-    if (j > 0) v = csub(v, e[x - L]);
-    if (j < g.h - 1) v = csub(v, e[x + L]);
-    if (j == 0) v = cadd(v, cb[(long long)c * n + x]);
-    if (j == g.h - 1) v = cadd(v, ct[(long long)c * n + x]);
-    long long idx = j * L + (long long)c * n + x;
+    const double d = fma(-(g.k * g.k), eps[(long long)j * n + x], 4.0);
+    const int xr = (x + 1 == n) ? 0 : x + 1, xl = (x == 0) ? n - 1 : x - 1;
+    double2 nbr = cadd(e[xr], e[xl]);  // neighbours minus boundary terms
+    if (j > 0) nbr = cadd(nbr, e[x - L]);
+    if (j < g.h - 1) nbr = cadd(nbr, e[x + L]);
+    if (j == 0) nbr = csub(nbr, cb[(long long)c * n + x]);
+    if (j == g.h - 1) nbr = csub(nbr, ct[(long long)c * n + x]);
+    const double2 ex = e[x];
+    const double2 v = make_double2(fma(d, ex.x, -nbr.x), fma(d, ex.y, -nbr.y));
+    const long long idx = j * L + (long long)c * n + x;
     r[idx] = R ? csub(R[idx], v) : v;  // without R: K E
 }
 
-// out[c] = sum_{j,x} |X_j[c][x]|^2 (one block per column, fixed order).
-__global__ void k_colnorm(const double2 *X, int h, int ncol, int nx, double *out) {
+// out[c] = sum_{j,x} |X_j[c][x]|^2 (one block of 256 threads per column, a
+// fixed summation order; two independent loads in flight per thread).  With
+// `copy`, X is also copied there.
+__global__ void __launch_bounds__(256) k_colnorm(const double2 *X, int h, int ncol, int nx, double *out,
+                                                 double2 *copy) {
     __shared__ double red[256];
-    int c = blockIdx.x;
-    double acc = 0.0;
+    const int c = blockIdx.x;
+    double a0 = 0.0, a1 = 0.0;
     for (int j = 0; j < h; ++j) {
-        const double2 *p = X + ((long long)j * ncol + c) * nx;
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) acc += cabs2(p[x]);
+        const long long o = ((long long)j * ncol + c) * nx;
+        const double2 *p = X + o;
+        int x = threadIdx.x;
+        for (; x + 256 < nx; x += 512) {
+            const double2 u = p[x], v = p[x + 256];
+            if (copy) {
+                copy[o + x] = u;
+                copy[o + x + 256] = v;
+            }
+            a0 += cabs2(u);
+            a1 += cabs2(v);
+        }
+        if (x < nx) {
+            const double2 u = p[x];
+            if (copy) copy[o + x] = u;
+            a0 += cabs2(u);
+        }
     }
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = a0 + a1;
     __syncthreads();
     for (int off = blockDim.x / 2; off > 0; off >>= 1) {
         if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
@@ -1249,9 +1271,8 @@ int mixed_fields_begin_b(const Bat &bt, cudaStream_t s) {
     for (int b = 0; b < bt.n; ++b) {
         apf_ctx *c = bt.c[b];
         const int ncol = c->cf + c->ca;
-        const long long total = (long long)ncol * c->nx * c->h;
-        cudaMemcpyAsync(c->d_R, c->d_Ew, sizeof(double2) * total, cudaMemcpyDeviceToDevice, s);
-        APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, c->d_R, c->h, ncol, c->nx, c->mw->rnorm);
+        // R = the right-hand side (kept for the residuals) and its column norms, in one pass
+        APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, (const double2 *)c->d_Ew, c->h, ncol, c->nx, c->mw->rnorm, c->d_R);
         R[b] = c->d_R;
         E[b] = c->d_Ew;
     }
@@ -1264,7 +1285,7 @@ static int resid_body(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
     int ncol = c->cf + c->ca;
     residual(c, c->d_Ew, w->r, s);
-    APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, c->nx, w->rnorm + ncol);
+    APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, c->nx, w->rnorm + ncol, (double2 *)nullptr);
     return APF_OK;
 }
 
@@ -1371,7 +1392,7 @@ static int mixed_refine_gmres(apf_ctx *c, cudaStream_t s) {
     cudaMemcpyAsync(nr.data(), w->rnorm, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
     for (;;) {
         residual(c, c->d_Ew, w->r, s);
-        APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, nx, w->rnorm + ncol);
+        APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, nx, w->rnorm + ncol, (double2 *)nullptr);
         cudaMemcpyAsync(ne.data(), w->rnorm + ncol, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return check_cuda(c, e, "refinement");
@@ -1397,7 +1418,8 @@ static int mixed_refine_gmres(apf_ctx *c, cudaStream_t s) {
                 APF_LAUNCH(c, k_coldot, ncol, 256, 0, s, w->KV + i * L, Wn, c->h, ncol, nx, hij);
                 APF_LAUNCH(c, k_colaxpy, fgrid, 256, 0, s, Wn, w->KV + i * L, hij, -1.0, ncol, nx);
             }
-            APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, Wn, c->h, ncol, nx, w->knrm + (long long)j * ncol);
+            APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, Wn, c->h, ncol, nx, w->knrm + (long long)j * ncol,
+                       (double2 *)nullptr);
             APF_LAUNCH(c, k_colscale, fgrid, 256, 0, s, Wn, Wn, w->knrm + (long long)j * ncol, ncol, nx);
         }
         cudaMemcpyAsync(hd.data(), w->kdot, sizeof(double2) * hd.size(), cudaMemcpyDeviceToHost, s);
