@@ -44,7 +44,6 @@ struct MixedWork {
     double2 *r = nullptr, *delta = nullptr;          // refinement buffers (h*ncol*nx)
     double2 *cb = nullptr, *ct = nullptr;            // circulant products on the boundary rows
     double *rnorm = nullptr;                         // ||R_c||^2, ||r_c||^2
-    double *cpart = nullptr;                         // per-row partial column norms, h*ncol
     int km = 0;                                      // GMRES(km) refinement (0: plain refinement)
     double2 *KV = nullptr, *KZ = nullptr;            // Krylov basis (km+1 fields) and preconditioned vectors (km)
     double2 *kdot = nullptr, *ky = nullptr;          // Gram-Schmidt coefficients (km+1)*km*ncol, update km*ncol
@@ -626,49 +625,40 @@ __global__ void k_residual(GridDev g, const double *eps, const double2 *E, const
     r[idx] = R ? csub(R[idx], v) : v;  // without R: K E
 }
 
-// Column norms out[c] = sum_{j,x} |X_j[c][x]|^2 in two passes with a fixed
-// summation order: k_colnorm_rows reduces one (column, row) pair per block
-// (256 threads, four independent loads in flight per thread) into
-// part[c * h + j], optionally copying X to `copy`; k_colnorm_sum adds the h
-// partials of a column in row order.
-__global__ void __launch_bounds__(256) k_colnorm_rows(const double2 *X, int h, int ncol, int nx, double *part,
-                                                      double2 *copy) {
+// out[c] = sum_{j,x} |X_j[c][x]|^2 (one block of 256 threads per column, a
+// fixed summation order; two independent loads in flight per thread).  With
+// `copy`, X is also copied there.
+__global__ void __launch_bounds__(256) k_colnorm(const double2 *X, int h, int ncol, int nx, double *out,
+                                                 double2 *copy) {
     __shared__ double red[256];
-    const int c = blockIdx.x, j = blockIdx.y;
-    const long long o = ((long long)j * ncol + c) * nx;
-    const double2 *p = X + o;
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
-    int x = threadIdx.x;
-    for (; x + 768 < nx; x += 1024) {
-        double2 u[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) u[q] = p[x + 256 * q];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (copy) copy[o + x + 256 * q] = u[q];
-            a[q] += cabs2(u[q]);
+    const int c = blockIdx.x;
+    double a0 = 0.0, a1 = 0.0;
+    for (int j = 0; j < h; ++j) {
+        const long long o = ((long long)j * ncol + c) * nx;
+        const double2 *p = X + o;
+        int x = threadIdx.x;
+        for (; x + 256 < nx; x += 512) {
+            const double2 u = p[x], v = p[x + 256];
+            if (copy) {
+                copy[o + x] = u;
+                copy[o + x + 256] = v;
+            }
+            a0 += cabs2(u);
+            a1 += cabs2(v);
+        }
+        if (x < nx) {
+            const double2 u = p[x];
+            if (copy) copy[o + x] = u;
+            a0 += cabs2(u);
         }
     }
-    for (; x < nx; x += 256) {
-        const double2 u = p[x];
-        if (copy) copy[o + x] = u;
-        a[0] += cabs2(u);
-    }
-    red[threadIdx.x] = (a[0] + a[1]) + (a[2] + a[3]);
+    red[threadIdx.x] = a0 + a1;
     __syncthreads();
     for (int off = blockDim.x / 2; off > 0; off >>= 1) {
         if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
         __syncthreads();
     }
-    if (threadIdx.x == 0) part[(long long)c * h + j] = red[0];
-}
-
-__global__ void k_colnorm_sum(const double *part, int h, int ncol, double *out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncol) return;
-    double acc = 0.0;
-    for (int j = 0; j < h; ++j) acc += part[(long long)c * h + j];
-    out[c] = acc;
+    if (threadIdx.x == 0) out[c] = red[0];
 }
 
 // Krylov helpers over fields [row][column][x]: per-column dot products
@@ -1055,14 +1045,6 @@ int approx_solve(apf_ctx *c, const double2 *Rin, double2 *Eout, int mcols, cudaS
     return approx_solve_b(one(c), &Rin, &Eout, mcols, s);
 }
 
-// Column norms of an h x ncol x nx field into out[0..ncol) (k_colnorm_rows,
-// k_colnorm_sum), optionally copying the field to `copy` on the way.
-static void colnorm(apf_ctx *c, const double2 *X, int ncol, double *out, double2 *copy, cudaStream_t s) {
-    MixedWork *w = c->mw;
-    APF_LAUNCH(c, k_colnorm_rows, dim3(ncol, c->h), 256, 0, s, X, c->h, ncol, c->nx, w->cpart, copy);
-    APF_LAUNCH(c, k_colnorm_sum, (ncol + 255) / 256, 256, 0, s, (const double *)w->cpart, c->h, ncol, out);
-}
-
 int residual(apf_ctx *c, const double2 *E, double2 *r, cudaStream_t s) {
     MixedWork *w = c->mw;
     int ncol = c->cf + c->ca;
@@ -1156,7 +1138,6 @@ int mixed_alloc(apf_ctx *c) {
     WA(w->r, h * ncol * n); WA(w->delta, h * ncol * n);
     WA(w->cb, ncol * n); WA(w->ct, ncol * n);
     WA(w->rnorm, 2 * ncol);
-    WA(w->cpart, h * ncol);
     w->km = c->krylov_m;
     if (w->km > 0) {
         WA(w->KV, (long long)(w->km + 1) * h * ncol * n);
@@ -1291,7 +1272,7 @@ int mixed_fields_begin_b(const Bat &bt, cudaStream_t s) {
         apf_ctx *c = bt.c[b];
         const int ncol = c->cf + c->ca;
         // R = the right-hand side (kept for the residuals) and its column norms, in one pass
-        colnorm(c, c->d_Ew, ncol, c->mw->rnorm, c->d_R, s);
+        APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, (const double2 *)c->d_Ew, c->h, ncol, c->nx, c->mw->rnorm, c->d_R);
         R[b] = c->d_R;
         E[b] = c->d_Ew;
     }
@@ -1304,7 +1285,7 @@ static int resid_body(apf_ctx *c, cudaStream_t s) {
     MixedWork *w = c->mw;
     int ncol = c->cf + c->ca;
     residual(c, c->d_Ew, w->r, s);
-    colnorm(c, w->r, ncol, w->rnorm + ncol, nullptr, s);
+    APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, c->nx, w->rnorm + ncol, (double2 *)nullptr);
     return APF_OK;
 }
 
@@ -1411,7 +1392,7 @@ static int mixed_refine_gmres(apf_ctx *c, cudaStream_t s) {
     cudaMemcpyAsync(nr.data(), w->rnorm, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
     for (;;) {
         residual(c, c->d_Ew, w->r, s);
-        colnorm(c, w->r, ncol, w->rnorm + ncol, nullptr, s);
+        APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, w->r, c->h, ncol, nx, w->rnorm + ncol, (double2 *)nullptr);
         cudaMemcpyAsync(ne.data(), w->rnorm + ncol, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return check_cuda(c, e, "refinement");
@@ -1437,7 +1418,8 @@ static int mixed_refine_gmres(apf_ctx *c, cudaStream_t s) {
                 APF_LAUNCH(c, k_coldot, ncol, 256, 0, s, w->KV + i * L, Wn, c->h, ncol, nx, hij);
                 APF_LAUNCH(c, k_colaxpy, fgrid, 256, 0, s, Wn, w->KV + i * L, hij, -1.0, ncol, nx);
             }
-            colnorm(c, Wn, ncol, w->knrm + (long long)j * ncol, nullptr, s);
+            APF_LAUNCH(c, k_colnorm, ncol, 256, 0, s, Wn, c->h, ncol, nx, w->knrm + (long long)j * ncol,
+                       (double2 *)nullptr);
             APF_LAUNCH(c, k_colscale, fgrid, 256, 0, s, Wn, Wn, w->knrm + (long long)j * ncol, ncol, nx);
         }
         cudaMemcpyAsync(hd.data(), w->kdot, sizeof(double2) * hd.size(), cudaMemcpyDeviceToHost, s);
