@@ -738,13 +738,14 @@ int tc_gemm_n(apf_ctx *c, int nprob, const TcProblem *pb, int nsplit, int M, int
     bool wide = (N > 128) && util(256) >= 0.7 * util(128);
     int bn = wide ? 256 : 128;
     long long ntiles = (long long)nprob * ((N + bn - 1) / bn) * ((M + BM - 1) / BM);
-    // leave a few SMs free so that kernels of other streams (concurrent designs'
-    // diagonal-block inversions, which cannot share an SM with a GEMM CTA) progress
+    // SMs left free for kernels of other streams: none by default, since the
+    // library runs one solve at a time per GPU and a stream's kernels follow
+    // each other (a caller that overlaps its own kernels may reserve some)
     static int reserve = -1;
     if (reserve < 0) {
-        const char *e = getenv("APF_GEMM_RESERVED_SMS");  // tuning knob; default 4
-        reserve = e ? atoi(e) : 4;
-        if (reserve < 0 || reserve > num_sms / 2) reserve = 4;
+        const char *e = getenv("APF_GEMM_RESERVED_SMS");  // tuning knob; default 0
+        reserve = e ? atoi(e) : 0;
+        if (reserve < 0 || reserve > num_sms / 2) reserve = 0;
         if (num_sms <= 64) reserve = 0;
     }
     unsigned grid = (unsigned)std::min<long long>(ntiles, num_sms - reserve);
