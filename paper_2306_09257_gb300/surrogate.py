@@ -12,7 +12,6 @@ computed from the exact S of the solver (mixed precision, refined).
 from __future__ import annotations
 
 import ctypes
-import threading
 import time
 from typing import Sequence
 
@@ -172,38 +171,35 @@ def design(w, seed: int) -> np.ndarray:
     return e
 
 
-def generate(w, seeds: Sequence[int], threads: int = 8, device: int = 0):
-    """Exact efficiencies for the designs of `seeds` (independent designs on
-    `threads` concurrent contexts).  Returns (eps float32 (N, h, nx) on the
-    device, targets float32 (N, 5) on the device, seconds)."""
+def generate(w, seeds: Sequence[int], batch: int = 16, device: int = 0):
+    """Exact efficiencies for the designs of `seeds`, `batch` designs per
+    apf_solve_S_grad_batch call (every launch shared by the batch; the
+    gradient it also returns is not used).  Returns (eps float32 (N, h, nx)
+    on the device, targets float32 (N, 5) on the device, seconds)."""
     seeds = list(seeds)
     dev = torch.device("cuda", device)
     X = torch.empty((len(seeds), w.h, w.nx), dtype=torch.float32, device=dev)
     T = torch.empty((len(seeds), len(ORDERS)), dtype=torch.float32, device=dev)
     t0 = time.perf_counter()
-
-    def work(k):
-        s = _apf.solver_for_workload(w, design(w, seeds[0]), precision="mixed", device=device)
-        mi, mo = s.channels()
-        idx = pair_index(mi, mo)
-        st = torch.cuda.Stream(device=dev)
-        with torch.cuda.stream(st):
-            S = torch.empty((len(mo), len(mi)), dtype=torch.complex128, device=dev)
-            for j in range(k, len(seeds), threads):
-                e = design(w, seeds[j])
-                s.set_eps(e, w.eps_sub, w.eps_clad, j0=w.j0)
-                s.solve_S(out=S)
-                T[j] = efficiencies(S, idx).float()
-                X[j] = torch.as_tensor(e, dtype=torch.float32, device=dev)
-        st.synchronize()
-        s.close()
-
-    ths = [threading.Thread(target=work, args=(k,)) for k in range(threads)]
-    for t in ths:
-        t.start()
-    for t in ths:
-        t.join()
+    nb = max(1, min(batch, len(seeds), 16))
+    sv = [_apf.solver_for_workload(w, design(w, seeds[0]), precision="mixed", device=device) for _ in range(nb)]
+    mi, mo = sv[0].channels()
+    idx = pair_index(mi, mo)
+    S = [torch.empty((len(mo), len(mi)), dtype=torch.complex128, device=dev) for _ in range(nb)]
+    G = [torch.empty((w.h, w.nx), dtype=torch.float64, device=dev) for _ in range(nb)]
+    for j0 in range(0, len(seeds), nb):
+        chunk = seeds[j0:j0 + nb]
+        for b, sd in enumerate(chunk):
+            e = design(w, sd)
+            sv[b].set_eps(e, w.eps_sub, w.eps_clad, j0=w.j0)
+            X[j0 + b] = torch.as_tensor(e, dtype=torch.float32, device=dev)
+        k = len(chunk)
+        _apf.solve_S_grad_batch(sv[:k], "power", ORDERS, 0.0, out_S=S[:k], out_grad=G[:k])
+        for b in range(k):
+            T[j0 + b] = efficiencies(S[b], idx).float()
     torch.cuda.synchronize()
+    for s in sv:
+        s.close()
     return X, T, time.perf_counter() - t0
 
 
@@ -249,12 +245,12 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--threads", type=int, default=8)
+    ap.add_argument("--batch-designs", type=int, default=16)
     ap.add_argument("--opt-iters", type=int, default=10)
     ap.add_argument("--starts", type=int, default=3)
     a = ap.parse_args(argv)
     w = W.MID
-    X, T, t_gen = generate(w, range(1_000_000, 1_000_000 + a.designs), threads=a.threads)
+    X, T, t_gen = generate(w, range(1_000_000, 1_000_000 + a.designs), batch=a.batch_designs)
     n_tr = a.designs - a.holdout
     sno = Surrogate(n=w.nx, in_ch=w.h, width=48, modes=64, layers=4, n_out=5, max_batch=256, seed=0)
     tr = train(sno, X[:n_tr], T[:n_tr], epochs=a.epochs, batch=a.batch, lr=a.lr)

@@ -67,7 +67,7 @@ def test_trained_surrogate_in_the_line_search(env):
     torch, SG = env
     from paper_2306_09257_gb300 import apf, optim, workloads as W
     w = W.MID
-    X, T, secs = SG.generate(w, range(10_000, 10_640), threads=8)
+    X, T, secs = SG.generate(w, range(10_000, 10_640), batch=16)
     sno = SG.Surrogate(n=w.nx, in_ch=w.h, width=48, modes=64, layers=4, n_out=5, max_batch=128, seed=0)
     tr, te = slice(0, 576), slice(576, 640)
     SG.train(sno, X[tr], T[tr], epochs=40, batch=64, lr=2e-3)
